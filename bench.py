@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the reduced-space SGM + per-pixel Kalman path.
+
+Workload (per GPU): B seeded synthetic stereo streams shaped like the paper's
+KITTI raw sequences -- 1242 x 375 uint8, f = 721 px, baseline 0.54 m, 128
+disparities, ego-motion about 1 m/frame with at most 1 degree of yaw per frame,
+ground plane + 20 boxes (3 moving).  Frame 0 of every stream is a full-range
+frame (untimed); each step is one reduced frame (fixed +-r windows, 8 paths,
+Kalman update and gate) of all B streams.  Inputs are resident in HBM before
+the timed region; the per-step working set (ragged cost and aggregated volumes,
+about 0.7 GB at B = 32) is larger than the 129 MB L2.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the oracle (the
+plain CPU restatement of the method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H, D, F, BASE = 1242, 375, 128, 721.0, 0.54
+N_PATHS = 8
+METRIC = "frames/s and cost-cell updates/s at 1242x375 vs plain form; p99 latency"
+# Algorithmic integer operations of one Eq. 1 update at one (pixel, disparity,
+# direction): + C, two + P1, three min (d, d-1, d+1 against m + P2), - m, the
+# running minimum for the next pixel, + into S.
+OPS_PER_CELL_PATH = 9
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from the committed ncu capture (None until one matches the kernel).
+NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=32, help="camera streams per GPU")
+    ap.add_argument("--radius", type=int, default=4)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-form, latency, e2e and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_inputs(B, nframes, seed0, device):
+    import torch
+    import synth
+    Ls, Rs, Ms, Ts = [], [], [], []
+    K = None
+    for b in range(B):
+        s = synth.kitti_like_sequence(seed0 + b, n_frames=max(100, nframes), width=W, height=H, f=F,
+                                      baseline=BASE, device=device, render_frames=nframes)
+        Ls.append(s["left"])
+        Rs.append(s["right"])
+        Ms.append(s["R"])
+        Ts.append(s["t"])
+        K = s["K"]
+    # [F, B, H, W] so that one frame of all streams is contiguous
+    left = torch.stack(Ls, 1).contiguous()
+    right = torch.stack(Rs, 1).contiguous()
+    return left, right, torch.stack(Ms, 1).contiguous(), torch.stack(Ts, 1).contiguous(), K
+
+
+# ------------------------------------------------------------------ reference arm: the oracle
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    n = 1 + args.warmup + args.steps
+    s = synth.kitti_like_sequence(1000, n_frames=max(100, n), width=W, height=H, f=F, baseline=BASE,
+                                  render_frames=n)
+    P = oracle.Params(W, H, max_disp=D, radius=args.radius)
+    L, R = s["left"].numpy(), s["right"].numpy()
+    o = oracle.frame(P, L[0], R[0])
+    times, cells = [], 0
+    for k in range(1, n):
+        t0 = time.perf_counter()
+        o = oracle.frame(P, L[k], R[k], state=(o["d"], o["p"]),
+                         motion=(s["R"][k].numpy(), s["t"][k].numpy(), s["K"].numpy(), BASE))
+        dt = time.perf_counter() - t0
+        if k > args.warmup:
+            times.append(dt)
+            cells += o["ncells"]
+    total = sum(times)
+    fps = len(times) / total
+    sample = "one 1242x375 stream, reduced frames %d..%d (r=%d, 8 paths), single thread" % (
+        args.warmup + 1, n - 1, args.radius)
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic",
+            "config": {"workload": "kitti-shaped stereo 1242x375, D=128, r=%d, 8 paths" % args.radius,
+                       "streams": 1, "sample": sample},
+            "cell_updates_per_s": cells * N_PATHS / total,
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, left, right, Rm, tv, K, budget_s=12.0):
+    """The oracle as it stands, timed on this host on stream 0 of the workload."""
+    import oracle
+    P = oracle.Params(W, H, max_disp=D, radius=args.radius)
+    L = left[:, 0].cpu().numpy()
+    R = right[:, 0].cpu().numpy()
+    o = oracle.frame(P, L[0], R[0])
+    times = []
+    k = 1
+    t_start = time.perf_counter()
+    while k < L.shape[0] and (time.perf_counter() - t_start < budget_s or len(times) < 3):
+        t0 = time.perf_counter()
+        o = oracle.frame(P, L[k], R[k], state=(o["d"], o["p"]),
+                         motion=(Rm[k, 0].numpy(), tv[k, 0].numpy(), K.numpy(), BASE))
+        times.append(time.perf_counter() - t0)
+        k += 1
+    fps = len(times) / sum(times)
+    return {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "stream 0, reduced frames 1..%d (r=%d, 8 paths), single thread" % (len(times), args.radius)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_1809_07986_gb300 as rs
+    from paper_1809_07986_gb300 import build as pkg_build
+
+    pkg_build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    B = args.batch
+    nframes = 1 + args.warmup + args.steps
+    left, right, Rm, tv, K = make_inputs(B, nframes, 1000 + 1000 * rank, dev)
+    stream = torch.cuda.Stream(dev)
+    P = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=B)
+    gs = rs.Stream(P, stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def run(h, frames, host=None, out=None):
+        for k in frames:
+            if host is None:
+                rs.rsgm_reduced_frame(h, left[k], right[k], Rm[k], tv[k], K, BASE)
+            else:
+                rs.rsgm_reduced_frame(h, host[0][k], host[1][k], Rm[k], tv[k], K, BASE)
+                rs.rsgm_state(h, out[0], None, out[1], None)
+
+    with torch.cuda.stream(stream):
+        gs.full_frame(left[0], right[0])
+        run(gs.handle, range(1, 1 + args.warmup))
+        gs.sync()
+        f0, c0, _ = gs.counters()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_rank) as clk:
+            ev0.record(stream)
+            run(gs.handle, range(1 + args.warmup, nframes))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        barrier()
+        f1, c1, _ = gs.counters()
+    steps = args.steps
+    frames_all = B * steps * world
+    cells_local = c1 - c0
+    cells_all = sum_over_ranks(cells_local)
+    value = frames_all / elapsed
+    result = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": steps,
+              "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+              "config": {"workload": "kitti-shaped stereo 1242x375, D=128, r=%d, 8 paths, %d seeded streams "
+                                     "per GPU, frames 1..%d of 100-frame sequences" % (args.radius, B, nframes - 1),
+                         "streams_per_gpu": B, "width": W, "height": H, "max_disp": D, "radius": args.radius,
+                         "paths": N_PATHS, "parallelism": "stream sharding, no collective" if world > 1 else "1 GPU",
+                         "l2": "per-step working set (ragged volumes) larger than L2"},
+              "cell_updates_per_s": cells_all * N_PATHS / elapsed,
+              "cells_per_frame": cells_local / (B * steps),
+              "gpu_launches": 15 * steps,
+              "clocks": clk.summary()}
+
+    # ---- dominant kernel: stage times with CUDA events on the launching stream
+    with torch.cuda.stream(stream):
+        rs.rsgm_enable_stage_timing(gs.handle, True)
+        gs.full_frame(left[0], right[0])
+        rs.rsgm_stage_times(gs.handle)
+        c_before = gs.counters()[1]
+        run(gs.handle, range(1, nframes))
+        st_ms, st_frames = rs.rsgm_stage_times(gs.handle)
+        c_after = gs.counters()[1]
+        rs.rsgm_enable_stage_timing(gs.handle, False)
+    cells_per_frame = (c_after - c_before) / max(st_frames, 1)
+    agg_ms = st_ms["aggregate"] / max(st_frames, 1)
+    total_ms = sum(st_ms.values()) / max(st_frames, 1)
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    # Derived integer peak: 152 SMs x 128 32-bit integer lanes x max SM clock.
+    int_peak_tops = 152 * 128 * sm_max * 1e6 / 1e12
+    achieved_tops = OPS_PER_CELL_PATH * cells_per_frame * N_PATHS / (agg_ms / 1e3) / 1e12
+    result["stage_ms_per_step"] = {k: v / max(st_frames, 1) for k, v in st_ms.items()}
+    result["roofline"] = {"kernel": "k_path (8 direction launches)", "bound": "alu", "achieved": achieved_tops,
+                          "peak": int_peak_tops, "unit": "Tops/s", "frac": achieved_tops / int_peak_tops,
+                          "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH,
+                          "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_max,
+                          "ops_per_cell_path": OPS_PER_CELL_PATH,
+                          "share_of_step": agg_ms / total_ms if total_ms else None}
+
+    if not args.no_extras:
+        # ---- e2e through the C ABI with host buffers (pinned), copies in the timed region
+        hl = left.cpu().pin_memory()
+        hr = right.cpu().pin_memory()
+        outd = torch.empty(B, H, W, dtype=torch.float32).pin_memory()
+        outm = torch.empty(B, H, W, dtype=torch.uint8).pin_memory()
+        with torch.cuda.stream(stream):
+            gs.full_frame(hl[0], hr[0])
+            run(gs.handle, range(1, 1 + args.warmup), host=(hl, hr), out=(outd, outm))
+            gs.sync()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run(gs.handle, range(1 + args.warmup, nframes), host=(hl, hr), out=(outd, outm))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        e2e_el = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        result["e2e"] = {"value": frames_all / e2e_el, "unit": "frames/s",
+                         "h2d_bytes_per_step": 2 * B * H * W, "d2h_bytes_per_step": B * H * W * 5}
+
+        # ---- plain form: full-range SGM + Kalman on every frame
+        Pp = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=B,
+                                    radius_mode=rs.RSGM_RADIUS_FULL)
+        gp = rs.Stream(Pp, stream)
+        nplain = min(5, steps)
+        with torch.cuda.stream(stream):
+            gp.full_frame(left[0], right[0])
+            run(gp.handle, range(1, 3))
+            gp.sync()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            run(gp.handle, range(3, 3 + nplain))
+            p1.record(stream)
+            torch.cuda.synchronize()
+        gp.close()
+        plain_el = max_over_ranks(p0.elapsed_time(p1) / 1e3)
+        plain_fps = B * nplain * world / plain_el
+        result["plain_form"] = {"value": plain_fps, "unit": "frames/s",
+                                "cell_updates_per_s": B * nplain * world * W * H * D * N_PATHS / plain_el,
+                                "speedup_of_reduced": value / plain_fps}
+
+        # ---- single-stream per-frame latency
+        P1s = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=1)
+        g1 = rs.Stream(P1s, stream)
+        lat = []
+        with torch.cuda.stream(stream):
+            g1.full_frame(left[0, 0], right[0, 0])
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(nframes - 1)]
+            for k in range(1, nframes):
+                evs[k - 1][0].record(stream)
+                rs.rsgm_reduced_frame(g1.handle, left[k, 0], right[k, 0], Rm[k, :1], tv[k, :1], K, BASE)
+                evs[k - 1][1].record(stream)
+            torch.cuda.synchronize()
+        lat = sorted(a.elapsed_time(b) for a, b in evs[args.warmup:] or evs)
+        g1.close()
+        q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+        result["latency_ms"] = {"p50": q(0.5), "p99": q(0.99), "frames": len(lat), "streams": 1}
+
+        if rank == 0:
+            result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)
+    gs.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * rsgm.h -- C ABI of the reduced-space SGM + per-pixel Kalman library (librsgm).
+ *
+ * The library runs, on one CUDA device, the per-frame path of "Computationally
+ * efficient dense moving object detection based on reduced space disparity
+ * estimation" (Popovic, Hadviger, Markovic, Petrovic):
+ *
+ *   1. prediction of the previous disparity and variance through the known
+ *      ego-motion (Section 2.4, Eqs. 2-4), zoom-hole filling and the
+ *      discontinuity reset (Section 2.4);
+ *   2. census transform and Hamming matching cost (Section 2.1) over a per-pixel
+ *      disparity window centred on the prediction ("two values for each pixel
+ *      that define the range for disparity search", Section 2);
+ *   3. multi-path cost aggregation, Eq. 1 (Section 2.2), and winner-takes-all
+ *      (Section 2.3);
+ *   4. the per-pixel scalar Kalman correction, Eqs. 5-6 (Section 2.4);
+ *   5. a per-pixel moving-object gate on the innovation (Section 4 detects
+ *      moving objects where predicted and measured disparity differ).
+ *
+ * A handle ("stream" below) holds B >= 1 camera streams of identical geometry
+ * (width, height, disparity range) that advance one frame per call, in
+ * lockstep; each has its own state and its own ego-motion.  All work is
+ * enqueued on the CUDA stream given at init; calls return before it finishes.
+ *
+ * Conventions.
+ *   - Images are uint8, row-major, pitch = width, stream-major:
+ *     element (b, y, x) at b*H*W + y*W + x.  Per-pixel outputs use the same
+ *     layout.
+ *   - Ego-motion of stream b: X_k = R_b X_{k-1} + t_b, metres, left-camera
+ *     frame (x right, y down, z forward); R_b row-major 3x3.  This is the
+ *     metric form of the paper's 4x4 H^k_{k-1} acting on (x, y, d, 1).
+ *   - K is the row-major 3x3 pinhole matrix [fx 0 cx; 0 fy cy; 0 0 1] of the
+ *     rectified left camera (zero skew); d = fx * baseline / Z; pixel centres
+ *     sit at integer coordinates.
+ *
+ * Pointers.  Image inputs and state outputs may be device pointers or host
+ * pointers (pinned or pageable); host data is copied through library-owned
+ * device buffers on the handle's stream.  With host outputs, call rsgm_sync
+ * before reading them.  Arrays passed by value (R, t, K) are copied during the
+ * call.  Input buffers must stay valid and unchanged until the enqueued work
+ * has completed.
+ *
+ * Errors.  Every function returns RSGM_OK (0) or a negative status.  Argument
+ * errors are detected before any work is enqueued and leave the handle
+ * unchanged.  Asynchronous device errors surface as RSGM_ERR_CUDA at a later
+ * call or at rsgm_sync; rsgm_last_error() gives a text description of the
+ * calling thread's most recent failure.
+ */
+#ifndef RSGM_H_
+#define RSGM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSGM_OK 0
+#define RSGM_ERR_INVALID_ARG (-1) /* bad pointer, size or parameter */
+#define RSGM_ERR_NO_STATE (-2)    /* reduced frame before any full frame / set_state */
+#define RSGM_ERR_OOM (-3)         /* device allocation failed at init */
+#define RSGM_ERR_CUDA (-4)        /* a CUDA runtime call or kernel failed */
+#define RSGM_ERR_TIMEOUT (-5)     /* reserved: a bounded device wait expired */
+#define RSGM_ERR_CHECK_FAILED (-6) /* a device-side consistency check failed */
+
+/* Search-window rule for pixels with a valid prediction (Section 2.4). */
+#define RSGM_RADIUS_FIXED 0     /* [c - radius, c + radius], c = round(d_pred) */
+#define RSGM_RADIUS_VARIANCE 1  /* half-width ceil(p_pred) clamped to [1, D]: the paper's d +- p */
+#define RSGM_RADIUS_FULL 2      /* whole range [0, D): plain SGM + Kalman ("plain form") */
+
+#define RSGM_MAX_BATCH 256
+#define RSGM_MAX_DISP 256
+
+typedef struct rsgm_stream_s *rsgm_stream; /* opaque, owned by the library */
+
+/*
+ * Parameters.  Paper-fixed defaults (Table 1): 5x5 census, P1 = 6, P2 = 65,
+ * 8 paths, 128 disparities.  The remaining defaults are readings of the
+ * paper: q = 0.15 px^2 (more than 99 % of ego-motion errors within +-1 px,
+ * Section 3.1), r_meas = 1 px^2, p_reset = D^2/12 (variance of a uniform
+ * distribution over the whole range, Section 2.4), tau_disc = 2 px,
+ * gate_gamma = 6.635 (chi-square, 1 degree of freedom, 99 %).
+ */
+typedef struct {
+    int32_t width, height;   /* pixels, >= 1 */
+    int32_t max_disp;        /* D: disparities 0 .. D-1, 1 <= D <= RSGM_MAX_DISP */
+    int32_t batch;           /* B camera streams per handle, 1 <= B <= RSGM_MAX_BATCH */
+    int32_t census_w, census_h; /* odd, <= 15, census_w * census_h - 1 <= 64 bits */
+    uint32_t path_mask;      /* bit i enables direction i; 0x0F non-diagonal, 0xF0 diagonal, 0xFF all */
+    int32_t radius_mode;     /* RSGM_RADIUS_* */
+    int32_t radius;          /* half-width for RSGM_RADIUS_FIXED, >= 0 */
+    int32_t P1, P2;          /* Eq. 1 penalties, 0 .. 4000 */
+    float q;                 /* process noise (Eq. 4), >= 0 */
+    float r_meas;            /* measurement noise (Eq. 6), > 0 */
+    float p_reset;           /* variance after a discontinuity reset; <= 0 selects D^2/12 */
+    float tau_disc;          /* discontinuity threshold, px, >= 0 */
+    float gate_gamma;        /* moving-object gate: nu^2 > gamma (p_pred + r_meas), > 0 */
+} rsgm_params;
+
+/* Path directions r = (dx, dy) by path_mask bit: the predecessor of p is p - r.
+ *   bit 0 (+1, 0)  bit 1 (-1, 0)  bit 2 (0, +1)  bit 3 (0, -1)
+ *   bit 4 (+1,+1)  bit 5 (-1,-1)  bit 6 (-1,+1)  bit 7 (+1,-1)            */
+
+/* Fills *p with the defaults above for a width x height, D = 128, B = 1
+ * stream.  Returns RSGM_ERR_INVALID_ARG if p is NULL. */
+int rsgm_default_params(rsgm_params *p, int32_t width, int32_t height);
+
+/*
+ * Creates a handle on the current CUDA device and allocates, once, every
+ * device buffer the path needs at its worst case (every pixel searching the
+ * whole range): about B*W*H*(3*D + 70) bytes.  cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream); all later work of the handle is
+ * enqueued on it.  Requires B*W*H*D < 2^32.  On error *out is set to NULL.
+ */
+int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream);
+
+/*
+ * The initial frame (Section 2.4, last paragraph: limits initially cover the
+ * whole search space, i.e. conventional SGM).  Every pixel searches [0, D);
+ * the state becomes d = d_z (the measurement), p = r_meas; the mask is 0.
+ * left, right: B*H*W uint8 each (device or host pointers).
+ */
+int rsgm_full_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right);
+
+/*
+ * One frame of the method for all B streams: predict the previous state
+ * through (R_b, t_b), search each pixel's window, aggregate (Eq. 1), take the
+ * winner, correct (Eqs. 5-6) and gate.  R: B*9 floats, t: B*3 floats, K: 9
+ * floats, all host memory, copied during the call; baseline in metres (> 0).
+ * Returns RSGM_ERR_NO_STATE if the handle has no state yet.
+ */
+int rsgm_reduced_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right,
+                       const float *R, const float *t, const float *K, float baseline);
+
+/*
+ * Copies the current state out: disparity d (float), variance p (float),
+ * moving-object mask (uint8, 1 = gated), integer winner (int16).  Each
+ * B*H*W elements; any pointer may be NULL to skip it; device or host memory.
+ */
+int rsgm_state(rsgm_stream s, float *disp, float *var, uint8_t *moving_mask, int16_t *disp_int);
+
+/* Imports a state (B*H*W floats each, device or host), e.g. to resume a
+ * checkpointed stream; the next rsgm_reduced_frame predicts from it. */
+int rsgm_set_state(rsgm_stream s, const float *disp, const float *var);
+
+/* Intermediate buffers of the most recent frame, for inspection and tests. */
+#define RSGM_BUF_CENSUS_L 0   /* uint64 per pixel */
+#define RSGM_BUF_CENSUS_R 1   /* uint64 per pixel */
+#define RSGM_BUF_WINDOW 2     /* uint32 per pixel: lo | (width << 16) */
+#define RSGM_BUF_OFFSET 3     /* uint32 per pixel: first cell of the pixel's window */
+#define RSGM_BUF_CLASS 4      /* uint8 per pixel: 0 predicted, 1 discontinuity reset, 2 no prediction */
+#define RSGM_BUF_D_PRED 5     /* float per pixel: predicted disparity (undefined where class 2) */
+#define RSGM_BUF_P_PRED 6     /* float per pixel: predicted variance (undefined where class 2) */
+#define RSGM_BUF_COST 7       /* uint8 per cell, N cells: ragged cost volume */
+#define RSGM_BUF_AGGREGATED 8 /* uint16 per cell: S, the sum over enabled paths of Eq. 1 */
+#define RSGM_BUF_D_MEAS 9     /* float per pixel: sub-pixel measurement d_z */
+#define RSGM_BUF_INNOVATION 10 /* float per pixel: d_z - d_pred (0 where class 2) */
+
+/* Copies buffer `which` into dst (device or host) if capacity >= its size;
+ * *bytes receives the size (may be queried with dst = NULL).  Synchronises
+ * the handle's stream. */
+int rsgm_read_buffer(rsgm_stream s, int which, void *dst, size_t capacity, size_t *bytes);
+
+/* Frames processed (summed over the B streams) and cost cells searched
+ * (summed over frames) since init; cells of the last frame.  Synchronises. */
+int rsgm_counters(rsgm_stream s, uint64_t *frames, uint64_t *cells, uint64_t *last_cells);
+
+/* Stage timing.  While enabled, every frame records CUDA events on the
+ * handle's stream around its stages: RSGM_STAGE_PREDICT (splat, hole fill,
+ * reset, window), _SCAN (cell offsets), _CENSUS, _COST, _AGGREGATE (all path
+ * directions, Eq. 1) and _UPDATE (winner, Kalman, gate).  Up to 4096 frames
+ * are kept; further frames are not timed. */
+#define RSGM_STAGE_PREDICT 0
+#define RSGM_STAGE_SCAN 1
+#define RSGM_STAGE_CENSUS 2
+#define RSGM_STAGE_COST 3
+#define RSGM_STAGE_AGGREGATE 4
+#define RSGM_STAGE_UPDATE 5
+#define RSGM_NUM_STAGES 6
+int rsgm_enable_stage_timing(rsgm_stream s, int enable);
+
+/* Synchronises, writes the milliseconds spent in each stage summed over the
+ * frames timed since the last call (ms: RSGM_NUM_STAGES doubles) and the
+ * number of frames to *frames, then starts a new accumulation. */
+int rsgm_stage_times(rsgm_stream s, double *ms, int32_t *frames);
+
+/* Waits for the handle's enqueued work; reports deferred device errors. */
+int rsgm_sync(rsgm_stream s);
+
+/* Waits for the handle's work and releases every resource.  NULL is a no-op. */
+int rsgm_destroy_stream(rsgm_stream s);
+
+/* Static text for a status code. */
+const char *rsgm_status_string(int code);
+
+/* Description of the calling thread's most recent failure ("" if none). */
+const char *rsgm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSGM_H_ */

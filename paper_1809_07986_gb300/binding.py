@@ -1,0 +1,240 @@
+"""Thin ctypes binding of librsgm (the C ABI declared in include/rsgm.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Functions keep the C names.  Tensors are passed by data pointer
+(device tensors, or host tensors for the host-buffer entry points); a
+non-zero status raises RsgmError.  The library must have been built
+(``paper_1809_07986_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+RSGM_OK = 0
+RSGM_ERR_INVALID_ARG = -1
+RSGM_ERR_NO_STATE = -2
+RSGM_ERR_OOM = -3
+RSGM_ERR_CUDA = -4
+RSGM_ERR_TIMEOUT = -5
+RSGM_ERR_CHECK_FAILED = -6
+
+RSGM_RADIUS_FIXED = 0
+RSGM_RADIUS_VARIANCE = 1
+RSGM_RADIUS_FULL = 2
+RSGM_MAX_BATCH = 256
+RSGM_MAX_DISP = 256
+
+RSGM_BUF_CENSUS_L = 0
+RSGM_BUF_CENSUS_R = 1
+RSGM_BUF_WINDOW = 2
+RSGM_BUF_OFFSET = 3
+RSGM_BUF_CLASS = 4
+RSGM_BUF_D_PRED = 5
+RSGM_BUF_P_PRED = 6
+RSGM_BUF_COST = 7
+RSGM_BUF_AGGREGATED = 8
+RSGM_BUF_D_MEAS = 9
+RSGM_BUF_INNOVATION = 10
+
+RSGM_STAGE_PREDICT = 0
+RSGM_STAGE_SCAN = 1
+RSGM_STAGE_CENSUS = 2
+RSGM_STAGE_COST = 3
+RSGM_STAGE_AGGREGATE = 4
+RSGM_STAGE_UPDATE = 5
+RSGM_NUM_STAGES = 6
+STAGE_NAMES = ("predict", "scan", "census", "cost", "aggregate", "update")
+
+
+class rsgm_params(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_disp", ctypes.c_int32),
+        ("batch", ctypes.c_int32), ("census_w", ctypes.c_int32), ("census_h", ctypes.c_int32),
+        ("path_mask", ctypes.c_uint32), ("radius_mode", ctypes.c_int32), ("radius", ctypes.c_int32),
+        ("P1", ctypes.c_int32), ("P2", ctypes.c_int32), ("q", ctypes.c_float), ("r_meas", ctypes.c_float),
+        ("p_reset", ctypes.c_float), ("tau_disc", ctypes.c_float), ("gate_gamma", ctypes.c_float),
+    ]
+
+
+class RsgmError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__("%s failed: %s (%d): %s" % (where, status_string(code), code, detail))
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes); matches include/rsgm.h
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "rsgm_default_params": (ctypes.c_int, [ctypes.POINTER(rsgm_params), ctypes.c_int32, ctypes.c_int32]),
+    "rsgm_init_stream": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(rsgm_params), _P]),
+    "rsgm_full_frame": (ctypes.c_int, [_P, _P, _P]),
+    "rsgm_reduced_frame": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_float]),
+    "rsgm_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "rsgm_set_state": (ctypes.c_int, [_P, _P, _P]),
+    "rsgm_read_buffer": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "rsgm_counters": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "rsgm_enable_stage_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "rsgm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    "rsgm_sync": (ctypes.c_int, [_P]),
+    "rsgm_destroy_stream": (ctypes.c_int, [_P]),
+    "rsgm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rsgm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads librsgm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError("librsgm.so is not built (%s); run paper_1809_07986_gb300.build.build() "
+                              "or __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().rsgm_status_string(code).decode()
+
+
+def last_error() -> str:
+    return lib().rsgm_last_error().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != RSGM_OK:
+        raise RsgmError(rc, where, last_error())
+
+
+def _ptr(x):
+    """Pointer of a tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to librsgm must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to librsgm must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("cannot pass %r to librsgm" % type(x))
+
+
+def _host_f32(x, n=None):
+    import numpy as np
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1))
+    if n is not None and a.size != n:
+        raise ValueError("expected %d floats, got %d" % (n, a.size))
+    return a
+
+
+# ------------------------------------------------------------------ the C entry points
+
+def rsgm_default_params(width: int, height: int, **overrides) -> rsgm_params:
+    p = rsgm_params()
+    _check(lib().rsgm_default_params(ctypes.byref(p), width, height), "rsgm_default_params")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError("rsgm_params has no field %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def rsgm_init_stream(params: rsgm_params, cuda_stream=None) -> int:
+    """Returns the handle (an int).  cuda_stream: a torch.cuda.Stream, a raw
+    cudaStream_t int, or None for the legacy default stream."""
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    h = _P()
+    _check(lib().rsgm_init_stream(ctypes.byref(h), ctypes.byref(params), cuda_stream), "rsgm_init_stream")
+    return h.value
+
+
+def rsgm_full_frame(h: int, left, right):
+    _check(lib().rsgm_full_frame(h, _ptr(left), _ptr(right)), "rsgm_full_frame")
+
+
+def rsgm_reduced_frame(h: int, left, right, R, t, K, baseline: float):
+    """R: B x 3 x 3, t: B x 3, K: 3 x 3 (host arrays or CPU tensors, float32),
+    B = the handle's batch."""
+    Ra = _host_f32(R)
+    if Ra.size == 0 or Ra.size % 9:
+        raise ValueError("R must hold B 3x3 matrices")
+    ta = _host_f32(t, Ra.size // 3)
+    Ka = _host_f32(K, 9)
+    _check(lib().rsgm_reduced_frame(h, _ptr(left), _ptr(right), _ptr(Ra), _ptr(ta), _ptr(Ka),
+                                    float(baseline)), "rsgm_reduced_frame")
+
+
+def rsgm_state(h: int, disp=None, var=None, moving_mask=None, disp_int=None):
+    _check(lib().rsgm_state(h, _ptr(disp), _ptr(var), _ptr(moving_mask), _ptr(disp_int)), "rsgm_state")
+
+
+def rsgm_set_state(h: int, disp, var):
+    _check(lib().rsgm_set_state(h, _ptr(disp), _ptr(var)), "rsgm_set_state")
+
+
+def rsgm_read_buffer(h: int, which: int, dst=None, capacity: int | None = None) -> int:
+    """Copies buffer `which` into dst (if given); returns its size in bytes."""
+    n = ctypes.c_size_t()
+    if capacity is None:
+        capacity = 0
+        if dst is not None:
+            capacity = dst.numel() * dst.element_size() if hasattr(dst, "numel") else dst.nbytes
+    _check(lib().rsgm_read_buffer(h, which, _ptr(dst), capacity, ctypes.byref(n)), "rsgm_read_buffer")
+    return n.value
+
+
+def rsgm_counters(h: int):
+    f, c, l = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().rsgm_counters(h, ctypes.byref(f), ctypes.byref(c), ctypes.byref(l)), "rsgm_counters")
+    return f.value, c.value, l.value
+
+
+def rsgm_enable_stage_timing(h: int, enable: bool = True):
+    _check(lib().rsgm_enable_stage_timing(h, 1 if enable else 0), "rsgm_enable_stage_timing")
+
+
+def rsgm_stage_times(h: int):
+    """Returns ({stage name: ms summed over timed frames}, frames)."""
+    ms = (ctypes.c_double * RSGM_NUM_STAGES)()
+    n = ctypes.c_int32()
+    _check(lib().rsgm_stage_times(h, ms, ctypes.byref(n)), "rsgm_stage_times")
+    return dict(zip(STAGE_NAMES, list(ms))), n.value
+
+
+def rsgm_sync(h: int):
+    _check(lib().rsgm_sync(h), "rsgm_sync")
+
+
+def rsgm_destroy_stream(h: int):
+    _check(lib().rsgm_destroy_stream(h), "rsgm_destroy_stream")
+
+
+def rsgm_status_string(code: int) -> str:
+    return status_string(code)
+
+
+def rsgm_last_error() -> str:
+    return last_error()

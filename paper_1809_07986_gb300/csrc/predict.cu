@@ -1,0 +1,291 @@
+// Prediction step of the per-pixel Kalman filter (Section 2.4 of the paper):
+// forward splat of the previous state through the ego-motion (Eqs. 2-4),
+// zoom-hole filling, discontinuity reset, the per-pixel search window and the
+// exclusive prefix sum that lays the windows out as a ragged cell volume.
+//
+// Floating-point values here decide integers (target pixel, window), so every
+// operation is an explicit round-to-nearest intrinsic in a fixed order; the
+// library is built with -fmad=false as a second guard against contraction.
+#include "rsgm_internal.cuh"
+
+namespace rsgm {
+namespace {
+
+constexpr unsigned kEmpty = 0u;  // key value of a pixel no point landed on
+
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// K1: every pixel with d > 0.5 is back-projected (Z = fx b / d), moved with
+// X' = R X + t and projected again (Eq. 2 in metric form).  The 64-bit key is
+// (bits of d' << 32) | (~source index): d' > 0, so positive-float bit patterns
+// order like the values and atomicMax keeps the nearest surface, breaking ties
+// toward the smaller source index.
+__global__ void __launch_bounds__(256) k_splat(const float *__restrict__ d,
+                                               unsigned long long *__restrict__ key,
+                                               const __grid_constant__ SplatArgs a)
+{
+    long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= a.g.NPIX) return;
+    int b = (int)(gi / a.g.HW);
+    int s = (int)(gi - (long long)b * a.g.HW);
+    int y = s / a.g.W, x = s - y * a.g.W;
+    float ds = d[gi];
+    if (!(ds > 0.5f)) return;
+    const Motion &m = a.m[b];
+    float Z = fdiv(a.fb, ds);
+    float X = fdiv(fmul(fsub((float)x, a.cx), Z), a.fx);
+    float Y = fdiv(fmul(fsub((float)y, a.cy), Z), a.fy);
+    float Xn = fadd(fadd(fadd(fmul(m.R[0], X), fmul(m.R[1], Y)), fmul(m.R[2], Z)), m.t[0]);
+    float Yn = fadd(fadd(fadd(fmul(m.R[3], X), fmul(m.R[4], Y)), fmul(m.R[5], Z)), m.t[1]);
+    float Zn = fadd(fadd(fadd(fmul(m.R[6], X), fmul(m.R[7], Y)), fmul(m.R[8], Z)), m.t[2]);
+    if (!(Zn > 0.0f)) return;
+    float xn = fadd(fdiv(fmul(a.fx, Xn), Zn), a.cx);
+    float yn = fadd(fdiv(fmul(a.fy, Yn), Zn), a.cy);
+    float dn = fdiv(a.fb, Zn);
+    if (!isfinite(dn)) return;
+    float xi = floorf(fadd(xn, 0.5f)), yi = floorf(fadd(yn, 0.5f));
+    if (!(xi >= 0.0f && xi <= (float)(a.g.W - 1) && yi >= 0.0f && yi <= (float)(a.g.H - 1)))
+        return;
+    long long tgt = (long long)b * a.g.HW + (long long)((int)yi * a.g.W + (int)xi);
+    unsigned long long k = ((unsigned long long)__float_as_uint(dn) << 32) |
+                           (unsigned long long)(0xFFFFFFFFu - (unsigned)s);
+    atomicMax(key + tgt, k);
+}
+
+// Decodes the splat that won pixel t of a stream and evaluates Eq. 3-4 for it.
+__device__ __forceinline__ bool winner(const unsigned long long *__restrict__ key,
+                                       const float *__restrict__ d, const float *__restrict__ p,
+                                       long long base, long long t, float q, float &dd, float &pp)
+{
+    unsigned long long k = key[base + t];
+    if (k == kEmpty) return false;
+    float dn = __uint_as_float((unsigned)(k >> 32));
+    unsigned src = 0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull);
+    float ds = d[base + src], ps = p[base + src];
+    float phi = fdiv(dn, ds);                        // Eq. 3
+    pp = fadd(fmul(fmul(phi, phi), ps), q);          // Eq. 4
+    dd = dn;
+    return true;
+}
+
+// K1b: prediction per target pixel, with zoom holes (no point landed) filled
+// from two known horizontal or two known vertical neighbours (both pairs:
+// average of four).  Unknown pixels get d_pred = -1.
+__global__ void __launch_bounds__(256) k_gather_fill(const unsigned long long *__restrict__ key,
+                                                     const float *__restrict__ d,
+                                                     const float *__restrict__ p,
+                                                     float *__restrict__ d_pred,
+                                                     float *__restrict__ p_pred, Geometry g, float q)
+{
+    long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.NPIX) return;
+    int b = (int)(gi / g.HW);
+    long long base = (long long)b * g.HW;
+    int s = (int)(gi - base);
+    int y = s / g.W, x = s - y * g.W;
+    float dd, pp;
+    if (winner(key, d, p, base, s, q, dd, pp)) {
+        d_pred[gi] = dd;
+        p_pred[gi] = pp;
+        return;
+    }
+    float dl = 0, pl = 0, dr = 0, pr = 0, du = 0, pu = 0, dw = 0, pw = 0;
+    bool h = x > 0 && x < g.W - 1 && winner(key, d, p, base, s - 1, q, dl, pl) &&
+             winner(key, d, p, base, s + 1, q, dr, pr);
+    bool v = y > 0 && y < g.H - 1 && winner(key, d, p, base, s - g.W, q, du, pu) &&
+             winner(key, d, p, base, s + g.W, q, dw, pw);
+    if (h && v) {
+        d_pred[gi] = fmul(fadd(fadd(dl, dr), fadd(du, dw)), 0.25f);
+        p_pred[gi] = fmul(fadd(fadd(pl, pr), fadd(pu, pw)), 0.25f);
+    } else if (h) {
+        d_pred[gi] = fmul(fadd(dl, dr), 0.5f);
+        p_pred[gi] = fmul(fadd(pl, pr), 0.5f);
+    } else if (v) {
+        d_pred[gi] = fmul(fadd(du, dw), 0.5f);
+        p_pred[gi] = fmul(fadd(pu, pw), 0.5f);
+    } else {
+        d_pred[gi] = -1.0f;
+        p_pred[gi] = 0.0f;
+    }
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x = 256, 8 warps);
+// the block total is written to `total` (shared).
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned &total)
+{
+    __shared__ unsigned warp_pre[8];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) warp_pre[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned w = lane < 8 ? warp_pre[lane] : 0u;
+        unsigned wi = w;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            unsigned n = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += n;
+        }
+        unsigned tot = __shfl_sync(0xffffffffu, wi, 7);
+        if (lane < 8) warp_pre[lane] = wi - w;
+        if (lane == 0) total = tot;
+    }
+    __syncthreads();
+    unsigned res = warp_pre[wid] + incl - v;
+    __syncthreads();
+    return res;
+}
+
+// K1c: one block per image row.  Discontinuity reset (a known pixel with a
+// known 4-neighbour more than tau_disc away keeps d but takes p_reset and the
+// full window), the search window, the in-row exclusive prefix sum of the
+// widths, the row total; also clears the splat keys for the next frame.
+__global__ void __launch_bounds__(256) k_window(float *__restrict__ d_pred, float *__restrict__ p_pred,
+                                                uint32_t *__restrict__ win, uint8_t *__restrict__ cls,
+                                                uint32_t *__restrict__ inrow,
+                                                uint32_t *__restrict__ row_total,
+                                                unsigned long long *__restrict__ key, Geometry g,
+                                                FrameParams fp)
+{
+    __shared__ unsigned total;
+    int row = blockIdx.x;  // b * H + y
+    int y = row % g.H;
+    long long rbase = (long long)row * g.W;
+    int chunk = (g.W + blockDim.x - 1) / blockDim.x;
+    int x0 = threadIdx.x * chunk;
+    int x1 = min(g.W, x0 + chunk);
+    unsigned local = 0;
+    for (int x = x0; x < x1; ++x) {
+        long long gi = rbase + x;
+        float dc = d_pred[gi];
+        int lo = 0, w = g.D;
+        uint8_t c = 2;
+        if (dc >= 0.0f) {
+            bool reset = false;
+            float dn;
+            if (x > 0 && (dn = d_pred[gi - 1]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
+            if (x < g.W - 1 && (dn = d_pred[gi + 1]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
+            if (y > 0 && (dn = d_pred[gi - g.W]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
+            if (y < g.H - 1 && (dn = d_pred[gi + g.W]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
+            if (reset) {
+                c = 1;
+            } else {
+                c = 0;
+                if (fp.radius_mode != RSGM_RADIUS_FULL) {
+                    int h;
+                    if (fp.radius_mode == RSGM_RADIUS_VARIANCE) {
+                        float cp = ceilf(p_pred[gi]);
+                        h = cp < 1.0f ? 1 : (cp > (float)g.D ? g.D : (int)cp);
+                    } else {
+                        h = fp.radius;
+                    }
+                    float cf = floorf(fadd(dc, 0.5f));
+                    int cc = cf < 0.0f ? 0 : (cf > (float)(g.D - 1) ? g.D - 1 : (int)cf);
+                    lo = max(0, cc - h);
+                    int hi = min(g.D - 1, cc + h);
+                    w = hi - lo + 1;
+                }
+            }
+        }
+        win[gi] = (uint32_t)lo | ((uint32_t)w << 16);
+        cls[gi] = c;
+        local += (unsigned)w;
+    }
+    // The reset variance is written only after every neighbour read of this
+    // row's d_pred (p_pred is not read by neighbours).
+    for (int x = x0; x < x1; ++x) {
+        long long gi = rbase + x;
+        if (cls[gi] == 1) p_pred[gi] = fp.p_reset;
+        key[gi] = 0ull;
+    }
+    unsigned pre = block_exclusive_scan(local, total);
+    for (int x = x0; x < x1; ++x) {
+        long long gi = rbase + x;
+        inrow[gi] = pre;
+        pre += win[gi] >> 16;
+    }
+    if (threadIdx.x == 0) row_total[row] = total;
+}
+
+// Initial frame: every pixel searches [0, D) and has no prediction.
+__global__ void __launch_bounds__(256) k_full_window(uint32_t *__restrict__ win, uint8_t *__restrict__ cls,
+                                                     uint32_t *__restrict__ inrow,
+                                                     uint32_t *__restrict__ row_total, Geometry g)
+{
+    long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.NPIX) return;
+    int x = (int)(gi % g.W);
+    win[gi] = (uint32_t)g.D << 16;
+    cls[gi] = 2;
+    inrow[gi] = (uint32_t)x * (uint32_t)g.D;
+    if (x == 0) row_total[gi / g.W] = (uint32_t)g.W * (uint32_t)g.D;
+}
+
+// Exclusive scan of the B*H row totals in one block; records the frame's cell
+// count in the counters.
+__global__ void __launch_bounds__(256) k_row_scan(const uint32_t *__restrict__ row_total,
+                                                  uint32_t *__restrict__ row_base, int nrows,
+                                                  int nstreams,
+                                                  unsigned long long *__restrict__ counters)
+{
+    __shared__ unsigned total;
+    int chunk = (nrows + blockDim.x - 1) / blockDim.x;
+    int r0 = threadIdx.x * chunk, r1 = min(nrows, r0 + chunk);
+    unsigned local = 0;
+    for (int r = r0; r < r1; ++r) local += row_total[r];
+    unsigned pre = block_exclusive_scan(local, total);
+    for (int r = r0; r < r1; ++r) {
+        row_base[r] = pre;
+        pre += row_total[r];
+    }
+    if (threadIdx.x == 0) {
+        counters[0] += (unsigned long long)nstreams;
+        counters[1] += total;
+        counters[2] = total;
+    }
+}
+
+unsigned blocks_for(long long n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace
+
+cudaError_t launch_splat(const Buffers &b, const SplatArgs &a, cudaStream_t st)
+{
+    k_splat<<<blocks_for(a.g.NPIX, 256), 256, 0, st>>>(b.d, b.key, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fill(const Buffers &b, const Geometry &g, float q, cudaStream_t st)
+{
+    k_gather_fill<<<blocks_for(g.NPIX, 256), 256, 0, st>>>(b.key, b.d, b.p, b.d_pred, b.p_pred, g, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window(const Buffers &b, const Geometry &g, const FrameParams &fp, cudaStream_t st)
+{
+    k_window<<<(unsigned)(g.B * g.H), 256, 0, st>>>(b.d_pred, b.p_pred, b.win, b.cls, b.inrow,
+                                                     b.row_total, b.key, g, fp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_full_window(const Buffers &b, const Geometry &g, cudaStream_t st)
+{
+    k_full_window<<<blocks_for(g.NPIX, 256), 256, 0, st>>>(b.win, b.cls, b.inrow, b.row_total, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, cudaStream_t st)
+{
+    k_row_scan<<<1, 256, 0, st>>>(b.row_total, b.row_base, g.B * g.H, g.B, b.counters);
+    return cudaGetLastError();
+}
+
+}  // namespace rsgm

@@ -1,0 +1,529 @@
+// C ABI of librsgm: handle life cycle, argument checks, buffer ownership and
+// the per-frame launch sequence (declared and documented in include/rsgm.h).
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "rsgm_internal.cuh"
+
+using namespace rsgm;
+
+constexpr int kMaxTimedFrames = 4096;
+
+// CUDA events around the stages of each timed frame.
+struct StageTimer {
+    bool on = false;
+    int n = 0;  // frames recorded since the last read
+    cudaEvent_t *ev = nullptr;  // kMaxTimedFrames * (RSGM_NUM_STAGES + 1)
+};
+
+struct rsgm_stream_s {
+    rsgm_params P;
+    StageTimer timer;
+    cudaStream_t st;
+    int device;
+    Geometry g;
+    int nbits;
+    float p_reset;
+    bool has_state;
+    Buffers buf;
+};
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(RSGM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RSGM_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_pointer(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_params(const rsgm_params *p)
+{
+    if (!p) return fail(RSGM_ERR_INVALID_ARG, "params is NULL");
+    if (p->width < 1 || p->height < 1 || p->width > 65535 || p->height > 65535)
+        return fail(RSGM_ERR_INVALID_ARG, "width/height must be in [1, 65535]");
+    if (p->max_disp < 1 || p->max_disp > RSGM_MAX_DISP)
+        return fail(RSGM_ERR_INVALID_ARG, "max_disp must be in [1, %d]", RSGM_MAX_DISP);
+    if (p->batch < 1 || p->batch > RSGM_MAX_BATCH)
+        return fail(RSGM_ERR_INVALID_ARG, "batch must be in [1, %d]", RSGM_MAX_BATCH);
+    if (p->census_w < 1 || p->census_h < 1 || !(p->census_w & 1) || !(p->census_h & 1) ||
+        p->census_w > 15 || p->census_h > 15 || p->census_w * p->census_h - 1 > 64)
+        return fail(RSGM_ERR_INVALID_ARG, "census window must be odd, <= 15 and have <= 64 bits");
+    if (p->path_mask == 0 || p->path_mask > 0xFFu)
+        return fail(RSGM_ERR_INVALID_ARG, "path_mask must enable 1..8 of the 8 directions");
+    if (p->radius_mode < RSGM_RADIUS_FIXED || p->radius_mode > RSGM_RADIUS_FULL)
+        return fail(RSGM_ERR_INVALID_ARG, "unknown radius_mode %d", p->radius_mode);
+    if (p->radius < 0) return fail(RSGM_ERR_INVALID_ARG, "radius must be >= 0");
+    if (p->P1 < 0 || p->P2 < 0 || p->P1 > 4000 || p->P2 > 4000)
+        return fail(RSGM_ERR_INVALID_ARG, "P1, P2 must be in [0, 4000]");
+    if (!(p->q >= 0.0f) || !(p->r_meas > 0.0f) || !(p->tau_disc >= 0.0f) || !(p->gate_gamma > 0.0f) ||
+        p->p_reset != p->p_reset)
+        return fail(RSGM_ERR_INVALID_ARG, "noise / threshold parameters out of range");
+    unsigned long long cells = (unsigned long long)p->batch * p->width * p->height * p->max_disp;
+    if (cells >= 0xFFFFFFFFull)
+        return fail(RSGM_ERR_INVALID_ARG, "batch*width*height*max_disp must be < 2^32");
+    return RSGM_OK;
+}
+
+template <typename T>
+int alloc(T **ptr, size_t count, void **all, int &nall)
+{
+    void *p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(T) ? count * sizeof(T) : 1) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RSGM_ERR_OOM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+    }
+    all[nall++] = p;
+    *ptr = (T *)p;
+    return RSGM_OK;
+}
+
+void free_buffers(Buffers &b)
+{
+    void *ptrs[] = {b.img_l, b.img_r, b.cen_l, b.cen_r, b.d,    b.p,    b.key,       b.d_pred,
+                    b.p_pred, b.win, b.cls,   b.inrow, b.off,  b.row_total, b.row_base, b.cost,
+                    b.S,    b.d_int, b.mask,  b.d_z,   b.nu,   b.counters};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    memset(&b, 0, sizeof(b));
+}
+
+FrameParams frame_params(const rsgm_stream_s *s)
+{
+    FrameParams fp;
+    fp.radius_mode = s->P.radius_mode;
+    fp.radius = s->P.radius;
+    fp.P1 = s->P.P1;
+    fp.P2 = s->P.P2;
+    fp.nbits = s->nbits;
+    fp.q = s->P.q;
+    fp.r_meas = s->P.r_meas;
+    fp.p_reset = s->p_reset;
+    fp.tau_disc = s->P.tau_disc;
+    fp.gamma = s->P.gate_gamma;
+    return fp;
+}
+
+// Copies a host image batch into the staging buffer; device pointers pass through.
+int stage_images(rsgm_stream s, const uint8_t *left, const uint8_t *right, const uint8_t **dl,
+                 const uint8_t **dr)
+{
+    size_t bytes = (size_t)s->g.NPIX;
+    *dl = left;
+    *dr = right;
+    if (!is_device_pointer(left)) {
+        RSGM_CUDA(cudaMemcpyAsync(s->buf.img_l, left, bytes, cudaMemcpyHostToDevice, s->st));
+        *dl = s->buf.img_l;
+    }
+    if (!is_device_pointer(right)) {
+        RSGM_CUDA(cudaMemcpyAsync(s->buf.img_r, right, bytes, cudaMemcpyHostToDevice, s->st));
+        *dr = s->buf.img_r;
+    }
+    return RSGM_OK;
+}
+
+// Records stage boundary `k` (0 = frame start) of the current timed frame.
+int mark(rsgm_stream s, int k)
+{
+    StageTimer &t = s->timer;
+    if (!t.on || t.n >= kMaxTimedFrames) return RSGM_OK;
+    RSGM_CUDA(cudaEventRecord(t.ev[t.n * (RSGM_NUM_STAGES + 1) + k], s->st));
+    if (k == RSGM_NUM_STAGES) t.n++;
+    return RSGM_OK;
+}
+
+#define RSGM_MARK(s, k)              \
+    do {                             \
+        int rc_ = mark((s), (k));    \
+        if (rc_) return rc_;         \
+    } while (0)
+
+// Census, cost, aggregation and the update: the part shared by both frame kinds.
+int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr)
+{
+    const Geometry &g = s->g;
+    FrameParams fp = frame_params(s);
+    RSGM_MARK(s, 1);
+    RSGM_CUDA(launch_row_scan(s->buf, g, s->st));
+    RSGM_MARK(s, 2);
+    RSGM_CUDA(launch_census(s->buf, g, dl, dr, s->P.census_w, s->P.census_h, s->st));
+    RSGM_MARK(s, 3);
+    RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
+    RSGM_MARK(s, 4);
+    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->st));
+    RSGM_MARK(s, 5);
+    RSGM_CUDA(launch_update(s->buf, g, fp, s->st));
+    RSGM_MARK(s, 6);
+    return RSGM_OK;
+}
+
+void destroy_timer(StageTimer &t)
+{
+    if (t.ev) {
+        for (int i = 0; i < kMaxTimedFrames * (RSGM_NUM_STAGES + 1); ++i)
+            if (t.ev[i]) cudaEventDestroy(t.ev[i]);
+        free(t.ev);
+    }
+    t.ev = nullptr;
+    t.on = false;
+    t.n = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rsgm_default_params(rsgm_params *p, int32_t width, int32_t height)
+{
+    if (!p) return fail(RSGM_ERR_INVALID_ARG, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    p->width = width;
+    p->height = height;
+    p->max_disp = 128;
+    p->batch = 1;
+    p->census_w = 5;
+    p->census_h = 5;
+    p->path_mask = 0xFFu;
+    p->radius_mode = RSGM_RADIUS_FIXED;
+    p->radius = 4;
+    p->P1 = 6;
+    p->P2 = 65;
+    p->q = 0.15f;
+    p->r_meas = 1.0f;
+    p->p_reset = 0.0f;  // -> D^2 / 12
+    p->tau_disc = 2.0f;
+    p->gate_gamma = 6.635f;
+    return RSGM_OK;
+}
+
+int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
+{
+    if (!out) return fail(RSGM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    rsgm_stream s = new (std::nothrow) rsgm_stream_s();
+    if (!s) return fail(RSGM_ERR_OOM, "host allocation failed");
+    s->P = *p;
+    s->st = (cudaStream_t)cuda_stream;
+    s->device = dev;
+    s->g.B = p->batch;
+    s->g.W = p->width;
+    s->g.H = p->height;
+    s->g.D = p->max_disp;
+    s->g.HW = (long long)p->width * p->height;
+    s->g.NPIX = s->g.HW * p->batch;
+    s->nbits = p->census_w * p->census_h - 1;
+    s->p_reset = p->p_reset > 0.0f ? p->p_reset : (float)p->max_disp * (float)p->max_disp / 12.0f;
+    s->has_state = false;
+    memset(&s->buf, 0, sizeof(s->buf));
+    Buffers &b = s->buf;
+    const size_t n = (size_t)s->g.NPIX, rows = (size_t)p->batch * p->height;
+    const size_t cells = n * (size_t)p->max_disp;
+    void *all[32];
+    int nall = 0;
+    if ((rc = alloc(&b.img_l, n, all, nall)) || (rc = alloc(&b.img_r, n, all, nall)) ||
+        (rc = alloc(&b.cen_l, n, all, nall)) || (rc = alloc(&b.cen_r, n, all, nall)) ||
+        (rc = alloc(&b.d, n, all, nall)) || (rc = alloc(&b.p, n, all, nall)) ||
+        (rc = alloc(&b.key, n, all, nall)) || (rc = alloc(&b.d_pred, n, all, nall)) ||
+        (rc = alloc(&b.p_pred, n, all, nall)) || (rc = alloc(&b.win, n, all, nall)) ||
+        (rc = alloc(&b.cls, n, all, nall)) || (rc = alloc(&b.inrow, n, all, nall)) ||
+        (rc = alloc(&b.off, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
+        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells, all, nall)) ||
+        (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
+        (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
+        (rc = alloc(&b.nu, n, all, nall)) || (rc = alloc(&b.counters, 4, all, nall))) {
+        free_buffers(b);
+        delete s;
+        return rc;
+    }
+    // Zero what later frames rely on: the splat keys and the counters; the
+    // remaining buffers are written before they are read.
+    if ((e = cudaMemsetAsync(b.key, 0, n * sizeof(unsigned long long), s->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned long long), s->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b.mask, 0, n, s->st)) != cudaSuccess) {
+        free_buffers(b);
+        delete s;
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    *out = s;
+    return RSGM_OK;
+}
+
+int rsgm_full_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right)
+{
+    if (!s || !left || !right) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or image");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    const uint8_t *dl, *dr;
+    int rc = stage_images(s, left, right, &dl, &dr);
+    if (rc) return rc;
+    RSGM_MARK(s, 0);
+    RSGM_CUDA(launch_full_window(s->buf, s->g, s->st));
+    rc = match_and_update(s, dl, dr);
+    if (rc) return rc;
+    s->has_state = true;
+    return RSGM_OK;
+}
+
+int rsgm_reduced_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right, const float *R,
+                       const float *t, const float *K, float baseline)
+{
+    if (!s || !left || !right || !R || !t || !K)
+        return fail(RSGM_ERR_INVALID_ARG, "NULL handle, image or motion array");
+    if (!(baseline > 0.0f) || !(K[0] > 0.0f) || !(K[4] > 0.0f) || K[1] != 0.0f || K[3] != 0.0f ||
+        K[6] != 0.0f || K[7] != 0.0f || K[8] != 1.0f)
+        return fail(RSGM_ERR_INVALID_ARG, "K must be [fx 0 cx; 0 fy cy; 0 0 1] with fx, fy > 0; baseline > 0");
+    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "reduced frame before any full frame or set_state");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    const uint8_t *dl, *dr;
+    int rc = stage_images(s, left, right, &dl, &dr);
+    if (rc) return rc;
+    // The argument block is large but copied at launch: no host buffer outlives the call.
+    SplatArgs *a = (SplatArgs *)malloc(sizeof(SplatArgs));
+    if (!a) return fail(RSGM_ERR_OOM, "host allocation failed");
+    a->g = s->g;
+    a->fx = K[0];
+    a->cx = K[2];
+    a->fy = K[4];
+    a->cy = K[5];
+    a->fb = K[0] * baseline;
+    a->q = s->P.q;
+    for (int b = 0; b < s->g.B; ++b) {
+        memcpy(a->m[b].R, R + 9 * b, 9 * sizeof(float));
+        memcpy(a->m[b].t, t + 3 * b, 3 * sizeof(float));
+    }
+    rc = mark(s, 0);
+    if (rc) {
+        free(a);
+        return rc;
+    }
+    cudaError_t e = launch_splat(s->buf, *a, s->st);
+    free(a);
+    if (e != cudaSuccess) return cuda_fail(e, "splat launch");
+    RSGM_CUDA(launch_gather_fill(s->buf, s->g, s->P.q, s->st));
+    FrameParams fp = frame_params(s);
+    RSGM_CUDA(launch_window(s->buf, s->g, fp, s->st));
+    return match_and_update(s, dl, dr);
+}
+
+int rsgm_state(rsgm_stream s, float *disp, float *var, uint8_t *moving_mask, int16_t *disp_int)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "no frame processed yet");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    size_t n = (size_t)s->g.NPIX;
+    if (disp) RSGM_CUDA(cudaMemcpyAsync(disp, s->buf.d, n * sizeof(float), cudaMemcpyDefault, s->st));
+    if (var) RSGM_CUDA(cudaMemcpyAsync(var, s->buf.p, n * sizeof(float), cudaMemcpyDefault, s->st));
+    if (moving_mask) RSGM_CUDA(cudaMemcpyAsync(moving_mask, s->buf.mask, n, cudaMemcpyDefault, s->st));
+    if (disp_int)
+        RSGM_CUDA(cudaMemcpyAsync(disp_int, s->buf.d_int, n * sizeof(int16_t), cudaMemcpyDefault, s->st));
+    return RSGM_OK;
+}
+
+int rsgm_set_state(rsgm_stream s, const float *disp, const float *var)
+{
+    if (!s || !disp || !var) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or state");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    size_t n = (size_t)s->g.NPIX;
+    RSGM_CUDA(cudaMemcpyAsync(s->buf.d, disp, n * sizeof(float), cudaMemcpyDefault, s->st));
+    RSGM_CUDA(cudaMemcpyAsync(s->buf.p, var, n * sizeof(float), cudaMemcpyDefault, s->st));
+    s->has_state = true;
+    return RSGM_OK;
+}
+
+int rsgm_read_buffer(rsgm_stream s, int which, void *dst, size_t capacity, size_t *bytes)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    size_t n = (size_t)s->g.NPIX;
+    const void *src = nullptr;
+    size_t size = 0;
+    if (which == RSGM_BUF_COST || which == RSGM_BUF_AGGREGATED) {
+        unsigned long long last = 0;
+        RSGM_CUDA(cudaMemcpyAsync(&last, s->buf.counters + 2, sizeof(last), cudaMemcpyDeviceToHost, s->st));
+        RSGM_CUDA(cudaStreamSynchronize(s->st));
+        if (which == RSGM_BUF_COST) {
+            src = s->buf.cost;
+            size = (size_t)last;
+        } else {
+            src = s->buf.S;
+            size = (size_t)last * sizeof(uint16_t);
+        }
+    } else {
+        switch (which) {
+        case RSGM_BUF_CENSUS_L: src = s->buf.cen_l; size = n * 8; break;
+        case RSGM_BUF_CENSUS_R: src = s->buf.cen_r; size = n * 8; break;
+        case RSGM_BUF_WINDOW: src = s->buf.win; size = n * 4; break;
+        case RSGM_BUF_OFFSET: src = s->buf.off; size = n * 4; break;
+        case RSGM_BUF_CLASS: src = s->buf.cls; size = n; break;
+        case RSGM_BUF_D_PRED: src = s->buf.d_pred; size = n * 4; break;
+        case RSGM_BUF_P_PRED: src = s->buf.p_pred; size = n * 4; break;
+        case RSGM_BUF_D_MEAS: src = s->buf.d_z; size = n * 4; break;
+        case RSGM_BUF_INNOVATION: src = s->buf.nu; size = n * 4; break;
+        default: return fail(RSGM_ERR_INVALID_ARG, "unknown buffer %d", which);
+        }
+    }
+    if (bytes) *bytes = size;
+    if (!dst) return RSGM_OK;
+    if (capacity < size) return fail(RSGM_ERR_INVALID_ARG, "capacity %zu < %zu bytes", capacity, size);
+    if (size) RSGM_CUDA(cudaMemcpyAsync(dst, src, size, cudaMemcpyDefault, s->st));
+    RSGM_CUDA(cudaStreamSynchronize(s->st));
+    return RSGM_OK;
+}
+
+int rsgm_counters(rsgm_stream s, uint64_t *frames, uint64_t *cells, uint64_t *last_cells)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    unsigned long long h[3];
+    RSGM_CUDA(cudaMemcpyAsync(h, s->buf.counters, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+    RSGM_CUDA(cudaStreamSynchronize(s->st));
+    if (frames) *frames = h[0];
+    if (cells) *cells = h[1];
+    if (last_cells) *last_cells = h[2];
+    return RSGM_OK;
+}
+
+int rsgm_enable_stage_timing(rsgm_stream s, int enable)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    StageTimer &t = s->timer;
+    if (enable && !t.ev) {
+        int total = kMaxTimedFrames * (RSGM_NUM_STAGES + 1);
+        t.ev = (cudaEvent_t *)calloc((size_t)total, sizeof(cudaEvent_t));
+        if (!t.ev) return fail(RSGM_ERR_OOM, "host allocation failed");
+        for (int i = 0; i < total; ++i) {
+            cudaError_t e = cudaEventCreate(&t.ev[i]);
+            if (e != cudaSuccess) {
+                destroy_timer(t);
+                return cuda_fail(e, "cudaEventCreate");
+            }
+        }
+    }
+    t.on = enable != 0;
+    t.n = 0;
+    return RSGM_OK;
+}
+
+int rsgm_stage_times(rsgm_stream s, double *ms, int32_t *frames)
+{
+    if (!s || !ms) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or output");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    RSGM_CUDA(cudaStreamSynchronize(s->st));
+    StageTimer &t = s->timer;
+    for (int k = 0; k < RSGM_NUM_STAGES; ++k) ms[k] = 0.0;
+    for (int f = 0; f < t.n; ++f) {
+        cudaEvent_t *e = t.ev + f * (RSGM_NUM_STAGES + 1);
+        for (int k = 0; k < RSGM_NUM_STAGES; ++k) {
+            float dt = 0.0f;
+            RSGM_CUDA(cudaEventElapsedTime(&dt, e[k], e[k + 1]));
+            ms[k] += dt;
+        }
+    }
+    if (frames) *frames = t.n;
+    t.n = 0;
+    return RSGM_OK;
+}
+
+int rsgm_sync(rsgm_stream s)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    RSGM_CUDA(cudaStreamSynchronize(s->st));
+    return RSGM_OK;
+}
+
+int rsgm_destroy_stream(rsgm_stream s)
+{
+    if (!s) return RSGM_OK;
+    int rc = RSGM_OK;
+    {
+        DeviceGuard dg(s->device);
+        cudaError_t e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+        free_buffers(s->buf);
+        destroy_timer(s->timer);
+    }
+    delete s;
+    return rc;
+}
+
+const char *rsgm_status_string(int code)
+{
+    switch (code) {
+    case RSGM_OK: return "ok";
+    case RSGM_ERR_INVALID_ARG: return "invalid argument";
+    case RSGM_ERR_NO_STATE: return "no state: run a full frame (or set_state) first";
+    case RSGM_ERR_OOM: return "device allocation failed";
+    case RSGM_ERR_CUDA: return "CUDA error";
+    case RSGM_ERR_TIMEOUT: return "device wait timed out";
+    case RSGM_ERR_CHECK_FAILED: return "device consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+const char *rsgm_last_error(void) { return g_last_error; }
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of librsgm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsgm.h"
+
+namespace rsgm {
+
+// Geometry of one handle: B streams of H x W pixels, D disparities.
+struct Geometry {
+    int B, W, H, D;
+    long long HW;    // pixels per stream
+    long long NPIX;  // B * HW
+};
+
+// Ego-motion of one stream: X_k = R X_{k-1} + t.
+struct Motion {
+    float R[9];
+    float t[3];
+};
+
+// Kernel argument block of the forward splat (passed by value; copied at launch).
+struct SplatArgs {
+    Geometry g;
+    float fx, fy, cx, cy, fb, q;
+    Motion m[RSGM_MAX_BATCH];
+};
+
+// Per-frame scalar parameters of the resolve / update kernels.
+struct FrameParams {
+    int radius_mode, radius;
+    int P1, P2, nbits;
+    float q, r_meas, p_reset, tau_disc, gamma;
+};
+
+// Device buffers owned by a handle (all sized at the worst case at init).
+struct Buffers {
+    uint8_t *img_l, *img_r;             // staging for host inputs, NPIX each
+    unsigned long long *cen_l, *cen_r;  // census codes, NPIX each
+    float *d, *p;                       // state, NPIX each
+    unsigned long long *key;            // splat z-buffer, NPIX, zero between frames
+    float *d_pred, *p_pred;             // prediction after hole fill / reset, NPIX each
+    uint32_t *win;                      // lo | width << 16, NPIX
+    uint8_t *cls;                       // 0 predicted, 1 reset, 2 no prediction
+    uint32_t *inrow;                    // exclusive offset within the pixel's row, NPIX
+    uint32_t *off;                      // first cell of the pixel, NPIX
+    uint32_t *row_total, *row_base;     // B*H each
+    uint8_t *cost;                      // ragged cost volume, NPIX * D
+    uint16_t *S;                        // ragged aggregated cost, NPIX * D
+    int16_t *d_int;
+    uint8_t *mask;
+    float *d_z, *nu;
+    unsigned long long *counters;       // [0] frames, [1] cells, [2] cells of the last frame
+};
+
+// ---- launchers (each returns the cudaError_t of its launch) ----
+
+// Prediction (Section 2.4): forward splat, hole fill, discontinuity reset,
+// window and in-row prefix sum; the row-total scan; the full-range window.
+cudaError_t launch_splat(const Buffers &b, const SplatArgs &a, cudaStream_t st);
+cudaError_t launch_gather_fill(const Buffers &b, const Geometry &g, float q, cudaStream_t st);
+cudaError_t launch_window(const Buffers &b, const Geometry &g, const FrameParams &fp, cudaStream_t st);
+cudaError_t launch_full_window(const Buffers &b, const Geometry &g, cudaStream_t st);
+cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, cudaStream_t st);
+
+// Matching (Section 2.1).
+cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *left,
+                          const uint8_t *right, int cw, int ch, cudaStream_t st);
+cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStream_t st);
+
+// Aggregation, Eq. 1 (Section 2.2): one launch per enabled direction.
+cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
+                         cudaStream_t st);
+
+// Winner-takes-all + Kalman correction + gate (Sections 2.3, 2.4).
+cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp,
+                          cudaStream_t st);
+
+}  // namespace rsgm

@@ -1,0 +1,90 @@
+// Winner-takes-all (Section 2.3 of the paper), parabola sub-pixel step, the
+// per-pixel Kalman correction (Eqs. 5-6, Section 2.4) and the moving-object
+// gate on the innovation, fused in one pass over the aggregated costs.
+#include "rsgm_internal.cuh"
+
+namespace rsgm {
+namespace {
+
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// K5: one thread per pixel.  d_int = first minimum of S over the window; with
+// both neighbours inside the window and den = S- - 2 S0 + S+ > 0 the
+// measurement is d_int + (S- - S+) / (2 den).  Pixels without a prediction
+// take the measurement (d = d_z, p = r).  Otherwise nu = d_z - d_pred; if
+// nu^2 > gamma (p_pred + r) the pixel is flagged and reset to the measurement,
+// else K = p_pred / (p_pred + r), d = d_pred + K nu,
+// p = (1 - K)^2 p_pred + K^2 r.
+__global__ void __launch_bounds__(256) k_update(const uint16_t *__restrict__ S,
+                                                const uint32_t *__restrict__ win,
+                                                const uint32_t *__restrict__ off,
+                                                const uint8_t *__restrict__ cls,
+                                                const float *__restrict__ d_pred,
+                                                const float *__restrict__ p_pred,
+                                                float *__restrict__ d, float *__restrict__ p,
+                                                int16_t *__restrict__ d_int, uint8_t *__restrict__ mask,
+                                                float *__restrict__ d_z, float *__restrict__ nu_out,
+                                                Geometry g, FrameParams fp)
+{
+    long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.NPIX) return;
+    uint32_t wv = win[gi];
+    int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
+    const uint16_t *s = S + off[gi];
+    int best = 0;
+    unsigned bs = s[0];
+    for (int k = 1; k < w; ++k) {
+        unsigned v = s[k];
+        if (v < bs) {
+            bs = v;
+            best = k;
+        }
+    }
+    int di = lo + best;
+    float dz = (float)di;
+    if (best >= 1 && best + 1 < w) {
+        int sm = s[best - 1], sp = s[best + 1];
+        int den = sm - 2 * (int)bs + sp;
+        if (den > 0) dz = fadd((float)di, fdiv((float)(sm - sp), (float)(2 * den)));
+    }
+    d_int[gi] = (int16_t)di;
+    d_z[gi] = dz;
+    float r = fp.r_meas;
+    if (cls[gi] == 2) {
+        d[gi] = dz;
+        p[gi] = r;
+        mask[gi] = 0;
+        nu_out[gi] = 0.0f;
+        return;
+    }
+    float dp = d_pred[gi], pv = p_pred[gi];
+    float v = fsub(dz, dp);
+    float sv = fadd(pv, r);
+    nu_out[gi] = v;
+    if (fmul(v, v) > fmul(fp.gamma, sv)) {
+        d[gi] = dz;
+        p[gi] = r;
+        mask[gi] = 1;
+        return;
+    }
+    float K = fdiv(pv, sv);
+    d[gi] = fadd(dp, fmul(K, v));
+    float omk = fsub(1.0f, K);
+    p[gi] = fadd(fmul(fmul(omk, omk), pv), fmul(fmul(K, K), r));
+    mask[gi] = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, cudaStream_t st)
+{
+    unsigned blocks = (unsigned)((g.NPIX + 255) / 256);
+    k_update<<<blocks, 256, 0, st>>>(b.S, b.win, b.off, b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int,
+                                     b.mask, b.d_z, b.nu, g, fp);
+    return cudaGetLastError();
+}
+
+}  // namespace rsgm

@@ -240,14 +240,16 @@ def tiny_pair(seed: int = 1, device="cpu"):
 
 def kitti_like_sequence(seed: int, n_frames: int = 100, width: int = 1242, height: int = 375,
                         f: float = 721.0, baseline: float = 0.54, n_boxes: int = 20, n_moving: int = 3,
-                        device="cpu"):
+                        device="cpu", render_frames: int | None = None):
     """A drive through a box-lined scene shaped like a KITTI raw sequence.
 
     Ego-motion: about 1 m/frame forward with a smooth yaw (at most 1 degree per
     frame).  Scene: ground plane (camera 1.65 m above it), a backdrop far enough
     that every disparity is >= 1, and n_boxes boxes on the ground, n_moving of
     which move on their own at 0.5-2 m/frame along the road.  Box faces stay at
-    least 4 m beside the path so that disparities stay below 128.
+    least 4 m beside the path so that disparities stay below 128.  Only the
+    first ``render_frames`` frames (default: all) are rendered; the scene and
+    motion are those of the n_frames-long sequence either way.
     """
     g = torch.Generator().manual_seed(seed)
 
@@ -274,8 +276,8 @@ def kitti_like_sequence(seed: int, n_frames: int = 100, width: int = 1242, heigh
         psis.append(psi_k)
         Rs.append(_yaw(psi_k))
         cs.append(pos.clone())
-    path_z = torch.stack(cs)[:, 2]
-    path_x = torch.stack(cs)[:, 0]
+    path_z = torch.stack(cs)[:, 2].contiguous()
+    path_x = torch.stack(cs)[:, 0].contiguous()
 
     def path_x_at(z):
         i = int(torch.clamp(torch.searchsorted(path_z, torch.tensor(float(z), dtype=torch.float64)), 0, n_frames - 1))
@@ -305,13 +307,14 @@ def kitti_like_sequence(seed: int, n_frames: int = 100, width: int = 1242, heigh
                   wall_texel=0.6)
     ngen = torch.Generator(device=device).manual_seed(seed + 7919)
     H, W = height, width
-    left = torch.empty(n_frames, H, W, dtype=torch.uint8, device=device)
+    nr = n_frames if render_frames is None else min(render_frames, n_frames)
+    left = torch.empty(nr, H, W, dtype=torch.uint8, device=device)
     right = torch.empty_like(left)
-    disp = torch.empty(n_frames, H, W, dtype=torch.float32, device=device)
-    Rm = torch.zeros(n_frames, 3, 3, dtype=torch.float32)
-    tv = torch.zeros(n_frames, 3, dtype=torch.float32)
+    disp = torch.empty(nr, H, W, dtype=torch.float32, device=device)
+    Rm = torch.zeros(nr, 3, 3, dtype=torch.float32)
+    tv = torch.zeros(nr, 3, dtype=torch.float32)
     Rm[0] = torch.eye(3)
-    for k in range(n_frames):
+    for k in range(nr):
         l, r, d = render(scene, rig, Rs[k], cs[k], k, 2.0, ngen, device)
         left[k], right[k], disp[k] = l, r, d
         if k > 0:
