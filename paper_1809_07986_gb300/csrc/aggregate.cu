@@ -3,19 +3,23 @@
 //   L_r(p,d) = C(p,d) + min(L_r(p-r,d), L_r(p-r,d+-1) + P1, m + P2) - m,
 //   m = min_k L_r(p-r,k) over the predecessor's window,
 // with L_r(p-r, .) = +inf outside that window and L_r = C at the first pixel
-// of a path.  S(p,d) is the sum of L_r over the enabled directions.
+// of a path.  Each enabled direction writes its own plane of L_r; the update
+// kernel sums the planes into S.
 //
-// One warp walks one path line; the cells of the current pixel's window are
-// spread over the lanes, the predecessor's losses sit in a per-warp shared
-// buffer indexed by absolute disparity, and the minimum m comes from one warp
-// reduction per pixel.  Directions run as consecutive launches: the first
-// enabled one writes S, the others add to it.
+// All enabled directions run in one launch.  A warp walks 32/G path lines at
+// once, G lanes per line (G = 8, 16 or 32, chosen from the window width):
+// the cells of the current pixel's window are spread over the G lanes (wider
+// windows loop in chunks of G), the predecessor's losses sit in a per-line
+// shared buffer indexed by absolute disparity, and m comes from a segmented
+// xor-shuffle reduction.  The pixel metadata (first cell, window) and the
+// first chunk of costs are fetched one to two pixels ahead.
 #include "rsgm_internal.cuh"
 
 namespace rsgm {
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr unsigned kFull = 0xffffffffu;
 
 // Start pixel (x, y) and length n of line j of direction (DX, DY).
 template <int DX, int DY>
@@ -32,110 +36,175 @@ __device__ __forceinline__ void line_start(int j, int W, int H, int &x, int &y, 
     } else {
         // diagonal: lines start on the row the direction enters from (j < W),
         // then on the column it enters from.
-        int yrow = DY > 0 ? 0 : H - 1;
-        int xcol = DX > 0 ? 0 : W - 1;
+        const int yrow = DY > 0 ? 0 : H - 1;
+        const int xcol = DX > 0 ? 0 : W - 1;
         if (j < W) {
             x = j;
             y = yrow;
-            int run_x = DX > 0 ? W - j : j + 1;
-            n = min(run_x, H);
+            n = min(DX > 0 ? W - j : j + 1, H);
         } else {
-            int k = j - W;                     // 0 .. H-2
-            y = DY > 0 ? k + 1 : k;            // the row-start line covers the corner
+            const int k = j - W;           // 0 .. H-2
+            y = DY > 0 ? k + 1 : k;        // the row-start line covers the corner
             x = xcol;
-            int run_y = DY > 0 ? H - y : y + 1;
-            n = min(W, run_y);
+            n = min(W, DY > 0 ? H - y : y + 1);
         }
     }
 }
 
-template <int DX, int DY>
-__device__ __forceinline__ int lines_per_stream(int W, int H)
+__host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, int H)
 {
-    return DY == 0 ? H : (DX == 0 ? W : W + H - 1);
+    return dy == 0 ? H : (dx == 0 ? W : W + H - 1);
 }
 
-template <int DX, int DY>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_path(const uint8_t *__restrict__ cost, uint16_t *__restrict__ S, const uint32_t *__restrict__ win,
-           const uint32_t *__restrict__ off, Geometry g, int P1, int P2, int first)
+// Walks the 32/G lines line0 .. line0 + 32/G - 1 of direction (DX, DY).
+template <int DX, int DY, int G, typename T>
+__device__ __forceinline__ void sweep(long long line0, const uint8_t *__restrict__ cost,
+                                      T *__restrict__ plane, const uint2 *__restrict__ meta,
+                                      const Geometry &g, int P1, int P2, uint16_t *wbuf)
 {
-    extern __shared__ uint16_t smem[];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int nl = lines_per_stream<DX, DY>(g.W, g.H);
-    long long line = (long long)blockIdx.x * kWarpsPerBlock + warp;
-    if (line >= (long long)g.B * nl) return;  // uniform per warp
-    int b = (int)(line / nl);
-    int j = (int)(line - (long long)b * nl);
-    int x, y, n;
-    line_start<DX, DY>(j, g.W, g.H, x, y, n);
-    uint16_t *buf0 = smem + warp * 2 * g.D;
-    uint16_t *buf1 = buf0 + g.D;
-    const long long base = (long long)b * g.HW;
+    const int lane = threadIdx.x & 31, seg = lane / G, sl = lane - seg * G;
+    const int nl = lines_per_stream(DX, DY, g.W, g.H);
+    const long long line = line0 + seg;
+    int n = 0;
+    long long p0 = 0;
+    if (line < (long long)g.B * nl) {
+        const int b = (int)(line / nl);
+        const int j = (int)(line - (long long)b * nl);
+        int x, y;
+        line_start<DX, DY>(j, g.W, g.H, x, y, n);
+        p0 = (long long)b * g.HW + (long long)y * g.W + x;
+    }
+    int nmax = n;
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+    const long long step = (long long)DY * g.W + DX;
+    uint16_t *bufA = wbuf + seg * 2 * g.D;
+    uint16_t *bufB = bufA + g.D;
+
+    uint2 mc = n > 0 ? meta[p0] : make_uint2(0u, 0u);
+    uint2 mn = n > 1 ? meta[p0 + step] : make_uint2(0u, 0u);
+    int c0 = (n > 0 && sl < (int)(mc.y >> 16)) ? (int)cost[mc.x + sl] : 0;
     int plo = 0, pw = 0, pmin = 0;
-    for (int i = 0; i < n; ++i, x += DX, y += DY) {
-        long long gp = base + (long long)y * g.W + x;
-        uint32_t wv = win[gp];
-        int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
-        uint32_t o = off[gp];
-        uint16_t *cur = (i & 1) ? buf1 : buf0;
-        const uint16_t *prv = (i & 1) ? buf0 : buf1;
-        unsigned lmin = 0xFFFFFFFFu;
-        for (int k = lane; k < w; k += 32) {
-            int d = lo + k;
-            int c = cost[o + k];
+    for (int i = 0; i < nmax; ++i) {
+        const uint2 mnn = (i + 2 < n) ? meta[p0 + (long long)(i + 2) * step] : make_uint2(0u, 0u);
+        const int cn = (i + 1 < n && sl < (int)(mn.y >> 16)) ? (int)cost[mn.x + sl] : 0;
+        const unsigned o = mc.x;
+        const int lo = (int)(mc.y & 0xFFFFu);
+        const int w = i < n ? (int)(mc.y >> 16) : 0;
+        uint16_t *cur = (i & 1) ? bufB : bufA;
+        const uint16_t *prv = (i & 1) ? bufA : bufB;
+        unsigned lmin = 0xFFFFu;
+        for (int k = sl; k < w; k += G) {
+            const int d = lo + k;
+            const int c = (k == sl) ? c0 : (int)cost[o + k];
             int L;
             if (i == 0) {
                 L = c;
             } else {
                 int best = pmin + P2;
-                int r = d - plo;
-                if (r >= 0 && r < pw) best = min(best, (int)prv[d]);
-                if (r - 1 >= 0 && r - 1 < pw) best = min(best, (int)prv[d - 1] + P1);
-                if (r + 1 >= 0 && r + 1 < pw) best = min(best, (int)prv[d + 1] + P1);
+                const int r = d - plo;
+                if ((unsigned)r < (unsigned)pw) best = min(best, (int)prv[d]);
+                if ((unsigned)(r - 1) < (unsigned)pw) best = min(best, (int)prv[d - 1] + P1);
+                if ((unsigned)(r + 1) < (unsigned)pw) best = min(best, (int)prv[d + 1] + P1);
                 L = c + best - pmin;
             }
             cur[d] = (uint16_t)L;
-            if (first)
-                S[o + k] = (uint16_t)L;
-            else
-                S[o + k] = (uint16_t)(S[o + k] + L);
+            plane[o + k] = (T)L;
             lmin = min(lmin, (unsigned)L);
         }
-        pmin = (int)__reduce_min_sync(0xffffffffu, lmin);
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
         __syncwarp();
+        pmin = (int)lmin;
         plo = lo;
         pw = w;
+        mc = mn;
+        mn = mnn;
+        c0 = cn;
     }
 }
 
-template <int DX, int DY>
-cudaError_t launch_dir(const Buffers &b, const Geometry &g, int P1, int P2, int first, cudaStream_t st)
+template <int G, typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_paths(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
+            const __grid_constant__ PathPlan plan)
 {
-    long long lines = (long long)g.B * (DY == 0 ? g.H : (DX == 0 ? g.W : g.W + g.H - 1));
-    unsigned blocks = (unsigned)((lines + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    size_t smem = (size_t)kWarpsPerBlock * 2 * g.D * sizeof(uint16_t);
-    k_path<DX, DY><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, b.S, b.win, b.off, g, P1, P2, first);
+    extern __shared__ uint16_t smem[];
+    const int warp = threadIdx.x >> 5;
+    const long long gw = (long long)blockIdx.x * kWarpsPerBlock + warp;
+    if (gw >= plan.warp_begin[plan.ndir]) return;  // uniform per warp
+    int s = 0;
+    while (s + 1 < plan.ndir && gw >= plan.warp_begin[s + 1]) ++s;
+    const long long line0 = (gw - plan.warp_begin[s]) * (32 / G);
+    uint16_t *wbuf = smem + warp * (32 / G) * 2 * plan.g.D;
+    T *plane = planes + (long long)plan.plane_of[s] * plan.plane_stride;
+    const Geometry &g = plan.g;
+    switch (plan.dir[s]) {
+    case 0: sweep<+1, 0, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    case 1: sweep<-1, 0, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    case 2: sweep<0, +1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    case 3: sweep<0, -1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    case 4: sweep<+1, +1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    case 5: sweep<-1, -1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    case 6: sweep<-1, +1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    default: sweep<+1, -1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
+    }
+}
+
+const int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
+const int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
+
+template <int G, typename T>
+cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
+{
+    const long long warps = plan.warp_begin[plan.ndir];
+    if (warps == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    const size_t smem = (size_t)kWarpsPerBlock * (32 / G) * 2 * plan.g.D * sizeof(uint16_t);
+    k_paths<G, T><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         cudaStream_t st)
+int lanes_per_line(int widest_narrow_window)
 {
-    typedef cudaError_t (*fn)(const Buffers &, const Geometry &, int, int, int, cudaStream_t);
-    static const fn dirs[8] = {launch_dir<+1, 0>,  launch_dir<-1, 0>,  launch_dir<0, +1>,
-                               launch_dir<0, -1>,  launch_dir<+1, +1>, launch_dir<-1, -1>,
-                               launch_dir<-1, +1>, launch_dir<+1, -1>};
-    int first = 1;
-    for (int i = 0; i < 8; ++i) {
-        if (!(path_mask & (1u << i))) continue;
-        cudaError_t e = dirs[i](b, g, P1, P2, first, st);
-        if (e != cudaSuccess) return e;
-        first = 0;
+    return widest_narrow_window <= 8 ? 8 : (widest_narrow_window <= 16 ? 16 : 32);
+}
+
+cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
+                         int lanes, int plane_bytes, cudaStream_t st)
+{
+    PathPlan plan;
+    plan.g = g;
+    plan.P1 = P1;
+    plan.P2 = P2;
+    plan.plane_stride = g.NPIX * (long long)g.D;
+    // Long lines first so that the tail of the launch is short: horizontal,
+    // diagonal, vertical.  Planes are numbered by direction bit order.
+    static const int order[8] = {0, 1, 4, 5, 6, 7, 2, 3};
+    int plane_index[8], np = 0;
+    for (int i = 0; i < 8; ++i) plane_index[i] = (path_mask & (1u << i)) ? np++ : -1;
+    plan.ndir = 0;
+    plan.warp_begin[0] = 0;
+    const int lines_per_warp = 32 / lanes;
+    for (int k = 0; k < 8; ++k) {
+        const int dir = order[k];
+        if (!(path_mask & (1u << dir))) continue;
+        const long long lines = (long long)g.B * lines_per_stream(kDX[dir], kDY[dir], g.W, g.H);
+        plan.dir[plan.ndir] = dir;
+        plan.plane_of[plan.ndir] = plane_index[dir];
+        plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + (lines + lines_per_warp - 1) / lines_per_warp;
+        plan.ndir++;
     }
-    return cudaSuccess;
+    if (plane_bytes == 1) {
+        if (lanes == 8) return launch_g<8, uint8_t>(b, plan, st);
+        if (lanes == 16) return launch_g<16, uint8_t>(b, plan, st);
+        return launch_g<32, uint8_t>(b, plan, st);
+    }
+    if (lanes == 8) return launch_g<8, uint16_t>(b, plan, st);
+    if (lanes == 16) return launch_g<16, uint16_t>(b, plan, st);
+    return launch_g<32, uint16_t>(b, plan, st);
 }
 
 }  // namespace rsgm

@@ -49,15 +49,15 @@ __global__ void __launch_bounds__(kTileX *kTileY) k_census(const uint8_t *__rest
     out[(long long)y * g.W + x] = code;
 }
 
-// K3: one thread per pixel.  Finalises the pixel's cell offset (row base +
-// in-row prefix) and writes C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)) for its
+// K3: one thread per pixel.  Finalises the pixel's metadata (first cell =
+// row base + in-row prefix, window) and writes C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)) for its
 // window; a match left of the image costs every census bit.
 __global__ void __launch_bounds__(256) k_cost(const unsigned long long *__restrict__ cen_l,
                                               const unsigned long long *__restrict__ cen_r,
                                               const uint32_t *__restrict__ win,
                                               const uint32_t *__restrict__ inrow,
                                               const uint32_t *__restrict__ row_base,
-                                              uint32_t *__restrict__ off, uint8_t *__restrict__ cost,
+                                              uint2 *__restrict__ meta, uint8_t *__restrict__ cost,
                                               Geometry g, int nbits)
 {
     long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,8 +65,8 @@ __global__ void __launch_bounds__(256) k_cost(const unsigned long long *__restri
     long long row = gi / g.W;
     int x = (int)(gi - row * g.W);
     uint32_t o = row_base[row] + inrow[gi];
-    off[gi] = o;
     uint32_t wv = win[gi];
+    meta[gi] = make_uint2(o, wv);
     int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
     unsigned long long cl = cen_l[gi];
     const unsigned long long *rr = cen_r + row * g.W;
@@ -89,7 +89,7 @@ cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *le
 cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStream_t st)
 {
     unsigned blocks = (unsigned)((g.NPIX + 255) / 256);
-    k_cost<<<blocks, 256, 0, st>>>(b.cen_l, b.cen_r, b.win, b.inrow, b.row_base, b.off, b.cost, g, nbits);
+    k_cost<<<blocks, 256, 0, st>>>(b.cen_l, b.cen_r, b.win, b.inrow, b.row_base, b.meta, b.cost, g, nbits);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,9 @@ struct rsgm_stream_s {
     int device;
     Geometry g;
     int nbits;
+    int nplanes;      // enabled path directions
+    int lanes;        // lanes per path line in the aggregation kernel
+    int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
     bool has_state;
     Buffers buf;
@@ -130,8 +133,8 @@ int alloc(T **ptr, size_t count, void **all, int &nall)
 void free_buffers(Buffers &b)
 {
     void *ptrs[] = {b.img_l, b.img_r, b.cen_l, b.cen_r, b.d,    b.p,    b.key,       b.d_pred,
-                    b.p_pred, b.win, b.cls,   b.inrow, b.off,  b.row_total, b.row_base, b.cost,
-                    b.S,    b.d_int, b.mask,  b.d_z,   b.nu,   b.counters};
+                    b.p_pred, b.win, b.cls,   b.inrow, b.meta, b.row_total, b.row_base, b.cost,
+                    b.planes, b.S,   b.d_int, b.mask,  b.d_z,  b.nu,   b.counters};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(&b, 0, sizeof(b));
@@ -199,9 +202,9 @@ int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr)
     RSGM_MARK(s, 3);
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
-    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->st));
+    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 5);
-    RSGM_CUDA(launch_update(s->buf, g, fp, s->st));
+    RSGM_CUDA(launch_update(s->buf, g, fp, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
     return RSGM_OK;
 }
@@ -266,6 +269,11 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
     s->g.HW = (long long)p->width * p->height;
     s->g.NPIX = s->g.HW * p->batch;
     s->nbits = p->census_w * p->census_h - 1;
+    s->nplanes = __builtin_popcount(p->path_mask);
+    s->plane_bytes = s->nbits + p->P2 <= 255 ? 1 : 2;
+    // Lanes per line: enough for the common (predicted) window; wider windows
+    // loop.  Full-range modes use a whole warp per line.
+    s->lanes = lanes_per_line(p->radius_mode == RSGM_RADIUS_FIXED ? 2 * p->radius + 1 : p->max_disp);
     s->p_reset = p->p_reset > 0.0f ? p->p_reset : (float)p->max_disp * (float)p->max_disp / 12.0f;
     s->has_state = false;
     memset(&s->buf, 0, sizeof(s->buf));
@@ -280,8 +288,9 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc(&b.key, n, all, nall)) || (rc = alloc(&b.d_pred, n, all, nall)) ||
         (rc = alloc(&b.p_pred, n, all, nall)) || (rc = alloc(&b.win, n, all, nall)) ||
         (rc = alloc(&b.cls, n, all, nall)) || (rc = alloc(&b.inrow, n, all, nall)) ||
-        (rc = alloc(&b.off, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
+        (rc = alloc(&b.meta, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
         (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells, all, nall)) ||
+        (rc = alloc((uint8_t **)&b.planes, cells * s->nplanes * s->plane_bytes, all, nall)) ||
         (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
         (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
         (rc = alloc(&b.nu, n, all, nall)) || (rc = alloc(&b.counters, 4, all, nall))) {
@@ -411,7 +420,15 @@ int rsgm_read_buffer(rsgm_stream s, int which, void *dst, size_t capacity, size_
         case RSGM_BUF_CENSUS_L: src = s->buf.cen_l; size = n * 8; break;
         case RSGM_BUF_CENSUS_R: src = s->buf.cen_r; size = n * 8; break;
         case RSGM_BUF_WINDOW: src = s->buf.win; size = n * 4; break;
-        case RSGM_BUF_OFFSET: src = s->buf.off; size = n * 4; break;
+        case RSGM_BUF_OFFSET: {
+            // first-cell field of the (first cell, window) pairs: a strided copy
+            if (bytes) *bytes = n * 4;
+            if (!dst) return RSGM_OK;
+            if (capacity < n * 4) return fail(RSGM_ERR_INVALID_ARG, "capacity %zu < %zu bytes", capacity, n * 4);
+            RSGM_CUDA(cudaMemcpy2DAsync(dst, 4, s->buf.meta, sizeof(uint2), 4, n, cudaMemcpyDefault, s->st));
+            RSGM_CUDA(cudaStreamSynchronize(s->st));
+            return RSGM_OK;
+        }
         case RSGM_BUF_CLASS: src = s->buf.cls; size = n; break;
         case RSGM_BUF_D_PRED: src = s->buf.d_pred; size = n * 4; break;
         case RSGM_BUF_P_PRED: src = s->buf.p_pred; size = n * 4; break;

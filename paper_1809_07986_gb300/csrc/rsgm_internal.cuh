@@ -28,6 +28,18 @@ struct SplatArgs {
     Motion m[RSGM_MAX_BATCH];
 };
 
+// Launch plan of the aggregation kernel: the enabled directions in launch
+// order, the first warp of each, and the plane each writes.
+struct PathPlan {
+    Geometry g;
+    int P1, P2;
+    int ndir;
+    int dir[8];
+    int plane_of[8];
+    long long warp_begin[9];
+    long long plane_stride;  // elements between consecutive planes
+};
+
 // Per-frame scalar parameters of the resolve / update kernels.
 struct FrameParams {
     int radius_mode, radius;
@@ -45,9 +57,10 @@ struct Buffers {
     uint32_t *win;                      // lo | width << 16, NPIX
     uint8_t *cls;                       // 0 predicted, 1 reset, 2 no prediction
     uint32_t *inrow;                    // exclusive offset within the pixel's row, NPIX
-    uint32_t *off;                      // first cell of the pixel, NPIX
+    uint2 *meta;                        // (first cell, window) of the pixel, NPIX
     uint32_t *row_total, *row_base;     // B*H each
     uint8_t *cost;                      // ragged cost volume, NPIX * D
+    void *planes;                       // one plane of L_r per enabled direction, NPIX * D each
     uint16_t *S;                        // ragged aggregated cost, NPIX * D
     int16_t *d_int;
     uint8_t *mask;
@@ -70,12 +83,15 @@ cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *le
                           const uint8_t *right, int cw, int ch, cudaStream_t st);
 cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStream_t st);
 
-// Aggregation, Eq. 1 (Section 2.2): one launch per enabled direction.
+// Aggregation, Eq. 1 (Section 2.2): every enabled direction in one launch,
+// `lanes` lanes per path line, planes of `plane_bytes` (1 or 2) per cell.
+int lanes_per_line(int widest_narrow_window);
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         cudaStream_t st);
+                         int lanes, int plane_bytes, cudaStream_t st);
 
-// Winner-takes-all + Kalman correction + gate (Sections 2.3, 2.4).
-cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp,
-                          cudaStream_t st);
+// Sum of the planes, winner-takes-all, Kalman correction and gate
+// (Sections 2.2-2.4).
+cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, int nplanes,
+                          int plane_bytes, cudaStream_t st);
 
 }  // namespace rsgm

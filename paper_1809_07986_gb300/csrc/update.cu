@@ -11,16 +11,18 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 
-// K5: one thread per pixel.  d_int = first minimum of S over the window; with
-// both neighbours inside the window and den = S- - 2 S0 + S+ > 0 the
-// measurement is d_int + (S- - S+) / (2 den).  Pixels without a prediction
-// take the measurement (d = d_z, p = r).  Otherwise nu = d_z - d_pred; if
-// nu^2 > gamma (p_pred + r) the pixel is flagged and reset to the measurement,
-// else K = p_pred / (p_pred + r), d = d_pred + K nu,
+// K5: one thread per pixel.  S(p,d) = sum of the direction planes (Section
+// 2.2), written out; d_int = first minimum of S over the window; with both
+// neighbours inside the window and den = S- - 2 S0 + S+ > 0 the measurement
+// is d_int + (S- - S+) / (2 den).  Pixels without a prediction take the
+// measurement (d = d_z, p = r).  Otherwise nu = d_z - d_pred; if
+// nu^2 > gamma (p_pred + r) the pixel is flagged and reset to the
+// measurement, else K = p_pred / (p_pred + r), d = d_pred + K nu,
 // p = (1 - K)^2 p_pred + K^2 r.
-__global__ void __launch_bounds__(256) k_update(const uint16_t *__restrict__ S,
-                                                const uint32_t *__restrict__ win,
-                                                const uint32_t *__restrict__ off,
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(const T *__restrict__ planes, long long plane_stride,
+                                                int nplanes, uint16_t *__restrict__ S,
+                                                const uint2 *__restrict__ meta,
                                                 const uint8_t *__restrict__ cls,
                                                 const float *__restrict__ d_pred,
                                                 const float *__restrict__ p_pred,
@@ -31,13 +33,15 @@ __global__ void __launch_bounds__(256) k_update(const uint16_t *__restrict__ S,
 {
     long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.NPIX) return;
-    uint32_t wv = win[gi];
-    int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
-    const uint16_t *s = S + off[gi];
+    const uint2 m = meta[gi];
+    const unsigned o = m.x;
+    const int lo = (int)(m.y & 0xFFFFu), w = (int)(m.y >> 16);
     int best = 0;
-    unsigned bs = s[0];
-    for (int k = 1; k < w; ++k) {
-        unsigned v = s[k];
+    unsigned bs = 0xFFFFFFFFu;
+    for (int k = 0; k < w; ++k) {
+        unsigned v = 0;
+        for (int q = 0; q < nplanes; ++q) v += planes[q * plane_stride + o + k];
+        S[o + k] = (uint16_t)v;
         if (v < bs) {
             bs = v;
             best = k;
@@ -46,7 +50,7 @@ __global__ void __launch_bounds__(256) k_update(const uint16_t *__restrict__ S,
     int di = lo + best;
     float dz = (float)di;
     if (best >= 1 && best + 1 < w) {
-        int sm = s[best - 1], sp = s[best + 1];
+        int sm = S[o + best - 1], sp = S[o + best + 1];
         int den = sm - 2 * (int)bs + sp;
         if (den > 0) dz = fadd((float)di, fdiv((float)(sm - sp), (float)(2 * den)));
     }
@@ -79,11 +83,19 @@ __global__ void __launch_bounds__(256) k_update(const uint16_t *__restrict__ S,
 
 }  // namespace
 
-cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, cudaStream_t st)
+cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, int nplanes,
+                          int plane_bytes, cudaStream_t st)
 {
     unsigned blocks = (unsigned)((g.NPIX + 255) / 256);
-    k_update<<<blocks, 256, 0, st>>>(b.S, b.win, b.off, b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int,
-                                     b.mask, b.d_z, b.nu, g, fp);
+    const long long stride = g.NPIX * (long long)g.D;
+    if (plane_bytes == 1)
+        k_update<uint8_t><<<blocks, 256, 0, st>>>((const uint8_t *)b.planes, stride, nplanes, b.S, b.meta,
+                                                  b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
+                                                  b.d_z, b.nu, g, fp);
+    else
+        k_update<uint16_t><<<blocks, 256, 0, st>>>((const uint16_t *)b.planes, stride, nplanes, b.S, b.meta,
+                                                   b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
+                                                   b.d_z, b.nu, g, fp);
     return cudaGetLastError();
 }
 
