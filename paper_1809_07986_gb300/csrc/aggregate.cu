@@ -12,7 +12,7 @@
 // windows loop in chunks of G), the predecessor's losses sit in a per-line
 // shared buffer indexed by absolute disparity, and m comes from a segmented
 // xor-shuffle reduction.  The pixel metadata (first cell, window) and the
-// first chunk of costs are fetched one to two pixels ahead.
+// first chunk of costs are fetched several pixels ahead.
 #include "rsgm_internal.cuh"
 
 namespace rsgm {
@@ -57,6 +57,11 @@ __host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, 
 }
 
 // Walks the 32/G lines line0 .. line0 + 32/G - 1 of direction (DX, DY).
+// Pixel metadata is fetched kAhead pixels ahead and the first chunk of
+// costs kAhead/2 pixels ahead, through a register ring (the pixel loop is
+// unrolled kAhead times so that ring slots are static registers).
+constexpr int kAhead = 8;
+
 template <int DX, int DY, int G, typename T>
 __device__ __forceinline__ void sweep(long long line0, const uint8_t *__restrict__ cost,
                                       T *__restrict__ plane, const uint2 *__restrict__ meta,
@@ -81,46 +86,63 @@ __device__ __forceinline__ void sweep(long long line0, const uint8_t *__restrict
     uint16_t *bufA = wbuf + seg * 2 * g.D;
     uint16_t *bufB = bufA + g.D;
 
-    uint2 mc = n > 0 ? meta[p0] : make_uint2(0u, 0u);
-    uint2 mn = n > 1 ? meta[p0 + step] : make_uint2(0u, 0u);
-    int c0 = (n > 0 && sl < (int)(mc.y >> 16)) ? (int)cost[mc.x + sl] : 0;
-    int plo = 0, pw = 0, pmin = 0;
-    for (int i = 0; i < nmax; ++i) {
-        const uint2 mnn = (i + 2 < n) ? meta[p0 + (long long)(i + 2) * step] : make_uint2(0u, 0u);
-        const int cn = (i + 1 < n && sl < (int)(mn.y >> 16)) ? (int)cost[mn.x + sl] : 0;
-        const unsigned o = mc.x;
-        const int lo = (int)(mc.y & 0xFFFFu);
-        const int w = i < n ? (int)(mc.y >> 16) : 0;
-        uint16_t *cur = (i & 1) ? bufB : bufA;
-        const uint16_t *prv = (i & 1) ? bufA : bufB;
-        unsigned lmin = 0xFFFFu;
-        for (int k = sl; k < w; k += G) {
-            const int d = lo + k;
-            const int c = (k == sl) ? c0 : (int)cost[o + k];
-            int L;
-            if (i == 0) {
-                L = c;
-            } else {
-                int best = pmin + P2;
-                const int r = d - plo;
-                if ((unsigned)r < (unsigned)pw) best = min(best, (int)prv[d]);
-                if ((unsigned)(r - 1) < (unsigned)pw) best = min(best, (int)prv[d - 1] + P1);
-                if ((unsigned)(r + 1) < (unsigned)pw) best = min(best, (int)prv[d + 1] + P1);
-                L = c + best - pmin;
-            }
-            cur[d] = (uint16_t)L;
-            plane[o + k] = (T)L;
-            lmin = min(lmin, (unsigned)L);
-        }
+    constexpr int kCostAhead = kAhead / 2;
+    uint2 mr[kAhead];
+    int cr[kAhead];
 #pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
-        __syncwarp();
-        pmin = (int)lmin;
-        plo = lo;
-        pw = w;
-        mc = mn;
-        mn = mnn;
-        c0 = cn;
+    for (int v = 0; v < kAhead; ++v) {
+        mr[v] = v < n ? meta[p0 + v * step] : make_uint2(0u, 0u);
+        cr[v] = 0;
+    }
+#pragma unroll
+    for (int v = 0; v < kCostAhead; ++v)
+        if (v < n && sl < (int)(mr[v].y >> 16)) cr[v] = cost[mr[v].x + sl];
+
+    int plo = 0, pw = 0, pmin = 0;
+#pragma unroll 1
+    for (int i0 = 0; i0 < nmax; i0 += kAhead) {
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            const int i = i0 + u;
+            if (i >= nmax) break;  // uniform per warp
+            const uint2 mc = mr[u];
+            const int c0 = cr[u];
+            // refill: metadata of pixel i + kAhead, first cost chunk of i + kCostAhead
+            const int uc = (u + kCostAhead) % kAhead;
+            mr[u] = (i + kAhead < n) ? meta[p0 + (long long)(i + kAhead) * step] : make_uint2(0u, 0u);
+            cr[uc] = (i + kCostAhead < n && sl < (int)(mr[uc].y >> 16)) ? (int)cost[mr[uc].x + sl] : 0;
+
+            const unsigned o = mc.x;
+            const int lo = (int)(mc.y & 0xFFFFu);
+            const int w = i < n ? (int)(mc.y >> 16) : 0;
+            uint16_t *cur = (i & 1) ? bufB : bufA;
+            const uint16_t *prv = (i & 1) ? bufA : bufB;
+            unsigned lmin = 0xFFFFu;
+            for (int k = sl; k < w; k += G) {
+                const int d = lo + k;
+                const int c = (k == sl) ? c0 : (int)cost[o + k];
+                int L;
+                if (i == 0) {
+                    L = c;
+                } else {
+                    int best = pmin + P2;
+                    const int r = d - plo;
+                    if ((unsigned)r < (unsigned)pw) best = min(best, (int)prv[d]);
+                    if ((unsigned)(r - 1) < (unsigned)pw) best = min(best, (int)prv[d - 1] + P1);
+                    if ((unsigned)(r + 1) < (unsigned)pw) best = min(best, (int)prv[d + 1] + P1);
+                    L = c + best - pmin;
+                }
+                cur[d] = (uint16_t)L;
+                plane[o + k] = (T)L;
+                lmin = min(lmin, (unsigned)L);
+            }
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
+            __syncwarp();
+            pmin = (int)lmin;
+            plo = lo;
+            pw = w;
+        }
     }
 }
 
@@ -179,7 +201,7 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     plan.g = g;
     plan.P1 = P1;
     plan.P2 = P2;
-    plan.plane_stride = g.NPIX * (long long)g.D;
+    plan.plane_stride = plane_stride(g);
     // Long lines first so that the tail of the launch is short: horizontal,
     // diagonal, vertical.  Planes are numbered by direction bit order.
     static const int order[8] = {0, 1, 4, 5, 6, 7, 2, 3};

@@ -15,6 +15,10 @@ struct Geometry {
     long long NPIX;  // B * HW
 };
 
+// Elements between consecutive direction planes: the worst-case cell count,
+// rounded up so that every plane starts 16-element aligned.
+inline long long plane_stride(const Geometry &g) { return (g.NPIX * (long long)g.D + 15) / 16 * 16; }
+
 // Ego-motion of one stream: X_k = R X_{k-1} + t.
 struct Motion {
     float R[9];

@@ -11,37 +11,58 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 
-// K5: one thread per pixel.  S(p,d) = sum of the direction planes (Section
-// 2.2), written out; d_int = first minimum of S over the window; with both
-// neighbours inside the window and den = S- - 2 S0 + S+ > 0 the measurement
-// is d_int + (S- - S+) / (2 den).  Pixels without a prediction take the
-// measurement (d = d_z, p = r).  Otherwise nu = d_z - d_pred; if
-// nu^2 > gamma (p_pred + r) the pixel is flagged and reset to the
-// measurement, else K = p_pred / (p_pred + r), d = d_pred + K nu,
+constexpr int kUpdWarps = 4;
+
+// K5: one warp per 32 consecutive pixels.  Their cells are one contiguous
+// span of the ragged volume (offsets are a raster-order prefix sum), so the
+// warp first sums the direction planes cell by cell with coalesced loads,
+// S(p,d) = sum_r L_r(p,d) (Section 2.2), writes S and stages it in shared
+// memory; then each lane takes one pixel: d_int = first minimum of S over the
+// window; with both neighbours inside the window and den = S- - 2 S0 + S+ > 0
+// the measurement is d_int + (S- - S+) / (2 den).  Pixels without a
+// prediction take the measurement (d = d_z, p = r).  Otherwise
+// nu = d_z - d_pred; if nu^2 > gamma (p_pred + r) the pixel is flagged and
+// reset to the measurement, else K = p_pred / (p_pred + r), d = d_pred + K nu,
 // p = (1 - K)^2 p_pred + K^2 r.
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(const T *__restrict__ planes, long long plane_stride,
-                                                int nplanes, uint16_t *__restrict__ S,
-                                                const uint2 *__restrict__ meta,
-                                                const uint8_t *__restrict__ cls,
-                                                const float *__restrict__ d_pred,
-                                                const float *__restrict__ p_pred,
-                                                float *__restrict__ d, float *__restrict__ p,
-                                                int16_t *__restrict__ d_int, uint8_t *__restrict__ mask,
-                                                float *__restrict__ d_z, float *__restrict__ nu_out,
-                                                Geometry g, FrameParams fp)
+__global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__ planes, long long plane_stride,
+                                                        int nplanes, uint16_t *__restrict__ S,
+                                                        const uint2 *__restrict__ meta,
+                                                        const uint8_t *__restrict__ cls,
+                                                        const float *__restrict__ d_pred,
+                                                        const float *__restrict__ p_pred,
+                                                        float *__restrict__ d, float *__restrict__ p,
+                                                        int16_t *__restrict__ d_int, uint8_t *__restrict__ mask,
+                                                        float *__restrict__ d_z, float *__restrict__ nu_out,
+                                                        Geometry g, FrameParams fp)
 {
-    long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= g.NPIX) return;
-    const uint2 m = meta[gi];
-    const unsigned o = m.x;
-    const int lo = (int)(m.y & 0xFFFFu), w = (int)(m.y >> 16);
-    int best = 0;
-    unsigned bs = 0xFFFFFFFFu;
-    for (int k = 0; k < w; ++k) {
+    extern __shared__ uint16_t sS[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long gi0 = ((long long)blockIdx.x * kUpdWarps + warp) * 32;
+    if (gi0 >= g.NPIX) return;  // uniform per warp
+    const long long gi = gi0 + lane;
+    const bool valid = gi < g.NPIX;
+    const uint2 m = valid ? meta[gi] : make_uint2(0u, 0u);
+    const int lo = (int)(m.y & 0xFFFFu), w = valid ? (int)(m.y >> 16) : 0;
+    const unsigned span0 = __shfl_sync(0xffffffffu, m.x, 0);
+    const int nvalid = (int)min(32LL, g.NPIX - gi0);
+    const unsigned last_end = __shfl_sync(0xffffffffu, m.x + (unsigned)w, nvalid - 1);
+    const int span = (int)(last_end - span0);
+    uint16_t *stage = sS + warp * 32 * g.D;
+    for (int c = lane; c < span; c += 32) {
+        const long long cell = (long long)span0 + c;
         unsigned v = 0;
-        for (int q = 0; q < nplanes; ++q) v += planes[q * plane_stride + o + k];
-        S[o + k] = (uint16_t)v;
+        for (int q = 0; q < nplanes; ++q) v += planes[q * plane_stride + cell];
+        S[cell] = (uint16_t)v;
+        stage[c] = (uint16_t)v;
+    }
+    __syncwarp();
+    if (!valid) return;
+    const uint16_t *s = stage + (m.x - span0);
+    int best = 0;
+    unsigned bs = s[0];
+    for (int k = 1; k < w; ++k) {
+        const unsigned v = s[k];
         if (v < bs) {
             bs = v;
             best = k;
@@ -50,7 +71,7 @@ __global__ void __launch_bounds__(256) k_update(const T *__restrict__ planes, lo
     int di = lo + best;
     float dz = (float)di;
     if (best >= 1 && best + 1 < w) {
-        int sm = S[o + best - 1], sp = S[o + best + 1];
+        int sm = s[best - 1], sp = s[best + 1];
         int den = sm - 2 * (int)bs + sp;
         if (den > 0) dz = fadd((float)di, fdiv((float)(sm - sp), (float)(2 * den)));
     }
@@ -86,14 +107,21 @@ __global__ void __launch_bounds__(256) k_update(const T *__restrict__ planes, lo
 cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, int nplanes,
                           int plane_bytes, cudaStream_t st)
 {
-    unsigned blocks = (unsigned)((g.NPIX + 255) / 256);
-    const long long stride = g.NPIX * (long long)g.D;
+    const unsigned blocks = (unsigned)((g.NPIX + kUpdWarps * 32 - 1) / (kUpdWarps * 32));
+    const long long stride = plane_stride(g);
+    const size_t smem = (size_t)kUpdWarps * 32 * g.D * sizeof(uint16_t);
+    if (smem > 48 * 1024) {  // D > 192: opt in to the larger shared-memory carve-out
+        cudaError_t e = plane_bytes == 1
+            ? cudaFuncSetAttribute(k_update<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(k_update<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     if (plane_bytes == 1)
-        k_update<uint8_t><<<blocks, 256, 0, st>>>((const uint8_t *)b.planes, stride, nplanes, b.S, b.meta,
+        k_update<uint8_t><<<blocks, kUpdWarps * 32, smem, st>>>((const uint8_t *)b.planes, stride, nplanes, b.S, b.meta,
                                                   b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
                                                   b.d_z, b.nu, g, fp);
     else
-        k_update<uint16_t><<<blocks, 256, 0, st>>>((const uint16_t *)b.planes, stride, nplanes, b.S, b.meta,
+        k_update<uint16_t><<<blocks, kUpdWarps * 32, smem, st>>>((const uint16_t *)b.planes, stride, nplanes, b.S, b.meta,
                                                    b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
                                                    b.d_z, b.nu, g, fp);
     return cudaGetLastError();

@@ -54,7 +54,7 @@ def test_tiny_pair_full_then_reduced(rs, orc):
 ])
 def test_tiny_pair_parameter_variants(rs, orc, overrides):
     L, R, Rm, tv, K, b = tiny_batch([2])
-    P = rs.rsgm_default_params(384, 128, max_disp=64, radius=4, **overrides)
+    P = rs.rsgm_default_params(384, 128, **{"max_disp": 64, "radius": 4, **overrides})
     run_sequence(rs, orc, P, L, R, Rm, tv, K, b, 2)
 
 
