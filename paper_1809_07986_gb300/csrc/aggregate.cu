@@ -12,7 +12,7 @@
 // windows loop in chunks of G), the predecessor's losses sit in a per-line
 // shared buffer indexed by absolute disparity, and m comes from a segmented
 // xor-shuffle reduction.  The pixel metadata (first cell, window) and the
-// first chunk of costs are fetched several pixels ahead.
+// first chunk of costs are fetched ahead.
 #include "rsgm_internal.cuh"
 
 namespace rsgm {
@@ -20,34 +20,30 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kInf = 0x7FFF;  // larger than any loss; + P1 still fits an int
 
-// Start pixel (x, y) and length n of line j of direction (DX, DY).
-template <int DX, int DY>
-__device__ __forceinline__ void line_start(int j, int W, int H, int &x, int &y, int &n)
+// Start pixel (x, y) and length n of line j of direction (dx, dy).
+__device__ __forceinline__ void line_start(int dx, int dy, int j, int W, int H, int &x, int &y, int &n)
 {
-    if (DY == 0) {  // horizontal: one line per row
+    if (dy == 0) {  // horizontal: one line per row
         y = j;
-        x = DX > 0 ? 0 : W - 1;
+        x = dx > 0 ? 0 : W - 1;
         n = W;
-    } else if (DX == 0) {  // vertical: one line per column
+    } else if (dx == 0) {  // vertical: one line per column
         x = j;
-        y = DY > 0 ? 0 : H - 1;
+        y = dy > 0 ? 0 : H - 1;
         n = H;
+    } else if (j < W) {
+        // diagonal: lines start on the row the direction enters from ...
+        x = j;
+        y = dy > 0 ? 0 : H - 1;
+        n = min(dx > 0 ? W - j : j + 1, H);
     } else {
-        // diagonal: lines start on the row the direction enters from (j < W),
-        // then on the column it enters from.
-        const int yrow = DY > 0 ? 0 : H - 1;
-        const int xcol = DX > 0 ? 0 : W - 1;
-        if (j < W) {
-            x = j;
-            y = yrow;
-            n = min(DX > 0 ? W - j : j + 1, H);
-        } else {
-            const int k = j - W;           // 0 .. H-2
-            y = DY > 0 ? k + 1 : k;        // the row-start line covers the corner
-            x = xcol;
-            n = min(W, DY > 0 ? H - y : y + 1);
-        }
+        // ... then on the column it enters from (the row-start line covers the corner)
+        const int k = j - W;  // 0 .. H-2
+        y = dy > 0 ? k + 1 : k;
+        x = dx > 0 ? 0 : W - 1;
+        n = min(W, dy > 0 ? H - y : y + 1);
     }
 }
 
@@ -56,95 +52,76 @@ __host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, 
     return dy == 0 ? H : (dx == 0 ? W : W + H - 1);
 }
 
-// Walks the 32/G lines line0 .. line0 + 32/G - 1 of direction (DX, DY).
-// Pixel metadata is fetched kAhead pixels ahead and the first chunk of
-// costs kAhead/2 pixels ahead, through a register ring (the pixel loop is
-// unrolled kAhead times so that ring slots are static registers).
-constexpr int kAhead = 8;
-
-template <int DX, int DY, int G, typename T>
-__device__ __forceinline__ void sweep(long long line0, const uint8_t *__restrict__ cost,
+// Walks the 32/G lines line0 .. line0 + 32/G - 1 of direction (dx, dy).  The
+// direction is a run-time value so that one copy of this code serves all
+// eight (a per-direction copy overflows the instruction cache).  Metadata is
+// fetched two pixels ahead and the first chunk of costs one pixel ahead.
+template <int G, typename T>
+__device__ __forceinline__ void sweep(int dx, int dy, long long line0, const uint8_t *__restrict__ cost,
                                       T *__restrict__ plane, const uint2 *__restrict__ meta,
                                       const Geometry &g, int P1, int P2, uint16_t *wbuf)
 {
     const int lane = threadIdx.x & 31, seg = lane / G, sl = lane - seg * G;
-    const int nl = lines_per_stream(DX, DY, g.W, g.H);
+    const int nl = lines_per_stream(dx, dy, g.W, g.H);
     const long long line = line0 + seg;
     int n = 0;
-    long long p0 = 0;
+    const uint2 *mp = meta;
     if (line < (long long)g.B * nl) {
         const int b = (int)(line / nl);
         const int j = (int)(line - (long long)b * nl);
         int x, y;
-        line_start<DX, DY>(j, g.W, g.H, x, y, n);
-        p0 = (long long)b * g.HW + (long long)y * g.W + x;
+        line_start(dx, dy, j, g.W, g.H, x, y, n);
+        mp = meta + (long long)b * g.HW + (long long)y * g.W + x;
     }
     int nmax = n;
 #pragma unroll
     for (int o = G; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
-    const long long step = (long long)DY * g.W + DX;
+    const int step = dy * g.W + dx;
     uint16_t *bufA = wbuf + seg * 2 * g.D;
     uint16_t *bufB = bufA + g.D;
 
-    constexpr int kCostAhead = kAhead / 2;
-    uint2 mr[kAhead];
-    int cr[kAhead];
-#pragma unroll
-    for (int v = 0; v < kAhead; ++v) {
-        mr[v] = v < n ? meta[p0 + v * step] : make_uint2(0u, 0u);
-        cr[v] = 0;
-    }
-#pragma unroll
-    for (int v = 0; v < kCostAhead; ++v)
-        if (v < n && sl < (int)(mr[v].y >> 16)) cr[v] = cost[mr[v].x + sl];
-
+    uint2 mc = n > 0 ? mp[0] : make_uint2(0u, 0u);
+    uint2 mn = n > 1 ? mp[step] : make_uint2(0u, 0u);
+    int c0 = (n > 0 && sl < (int)(mc.y >> 16)) ? (int)cost[mc.x + sl] : 0;
     int plo = 0, pw = 0, pmin = 0;
-#pragma unroll 1
-    for (int i0 = 0; i0 < nmax; i0 += kAhead) {
-#pragma unroll
-        for (int u = 0; u < kAhead; ++u) {
-            const int i = i0 + u;
-            if (i >= nmax) break;  // uniform per warp
-            const uint2 mc = mr[u];
-            const int c0 = cr[u];
-            // refill: metadata of pixel i + kAhead, first cost chunk of i + kCostAhead
-            const int uc = (u + kCostAhead) % kAhead;
-            mr[u] = (i + kAhead < n) ? meta[p0 + (long long)(i + kAhead) * step] : make_uint2(0u, 0u);
-            cr[uc] = (i + kCostAhead < n && sl < (int)(mr[uc].y >> 16)) ? (int)cost[mr[uc].x + sl] : 0;
-
-            const unsigned o = mc.x;
-            const int lo = (int)(mc.y & 0xFFFFu);
-            const int w = i < n ? (int)(mc.y >> 16) : 0;
-            uint16_t *cur = (i & 1) ? bufB : bufA;
-            const uint16_t *prv = (i & 1) ? bufA : bufB;
-            unsigned lmin = 0xFFFFu;
-            for (int k = sl; k < w; k += G) {
-                const int d = lo + k;
-                const int c = (k == sl) ? c0 : (int)cost[o + k];
-                int L;
-                if (i == 0) {
-                    L = c;
-                } else {
-                    int best = pmin + P2;
-                    const int r = d - plo;
-                    if ((unsigned)r < (unsigned)pw) best = min(best, (int)prv[d]);
-                    if ((unsigned)(r - 1) < (unsigned)pw) best = min(best, (int)prv[d - 1] + P1);
-                    if ((unsigned)(r + 1) < (unsigned)pw) best = min(best, (int)prv[d + 1] + P1);
-                    L = c + best - pmin;
-                }
-                cur[d] = (uint16_t)L;
-                plane[o + k] = (T)L;
-                lmin = min(lmin, (unsigned)L);
-            }
-#pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
-            __syncwarp();
-            pmin = (int)lmin;
-            plo = lo;
-            pw = w;
+    for (int i = 0; i < nmax; ++i) {
+        mp += step;
+        const uint2 mnn = (i + 2 < n) ? mp[step] : make_uint2(0u, 0u);
+        const int cn = (i + 1 < n && sl < (int)(mn.y >> 16)) ? (int)cost[mn.x + sl] : 0;
+        const unsigned o = mc.x;
+        const int lo = (int)(mc.y & 0xFFFFu);
+        const int w = i < n ? (int)(mc.y >> 16) : 0;
+        uint16_t *cur = (i & 1) ? bufB : bufA;
+        const uint16_t *prv = (i & 1) ? bufA : bufB;
+        const int cap = i == 0 ? 0 : pmin + P2;
+        unsigned lmin = 0xFFFFu;
+        for (int k = sl; k < w; k += G) {
+            const int d = lo + k;
+            const int c = (k == sl) ? c0 : (int)cost[o + k];
+            const int r = d - plo;
+            const int p0v = (unsigned)r < (unsigned)pw ? (int)prv[d] : kInf;
+            const int pmv = (unsigned)(r - 1) < (unsigned)pw ? (int)prv[d - 1] : kInf;
+            const int ppv = (unsigned)(r + 1) < (unsigned)pw ? (int)prv[d + 1] : kInf;
+            const int L = c + min(min(p0v, cap), min(pmv, ppv) + P1) - pmin;
+            cur[d] = (uint16_t)L;
+            plane[o + k] = (T)L;
+            lmin = min(lmin, (unsigned)L);
         }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
+        __syncwarp();
+        pmin = (int)lmin;
+        plo = lo;
+        pw = w;
+        mc = mn;
+        mn = mnn;
+        c0 = cn;
     }
 }
+
+// Path directions by path_mask bit: the predecessor of p is p - (dx, dy).
+__constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
+__constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
 template <int G, typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -160,21 +137,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const long long line0 = (gw - plan.warp_begin[s]) * (32 / G);
     uint16_t *wbuf = smem + warp * (32 / G) * 2 * plan.g.D;
     T *plane = planes + (long long)plan.plane_of[s] * plan.plane_stride;
-    const Geometry &g = plan.g;
-    switch (plan.dir[s]) {
-    case 0: sweep<+1, 0, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    case 1: sweep<-1, 0, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    case 2: sweep<0, +1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    case 3: sweep<0, -1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    case 4: sweep<+1, +1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    case 5: sweep<-1, -1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    case 6: sweep<-1, +1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    default: sweep<+1, -1, G, T>(line0, cost, plane, meta, g, plan.P1, plan.P2, wbuf); break;
-    }
+    const int dir = plan.dir[s];
+    sweep<G, T>(kDX[dir], kDY[dir], line0, cost, plane, meta, plan.g, plan.P1, plan.P2, wbuf);
 }
 
-const int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
-const int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
 template <int G, typename T>
 cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
@@ -188,6 +154,9 @@ cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
 }
 
 }  // namespace
+
+const int kHostDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
+const int kHostDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
 int lanes_per_line(int widest_narrow_window)
 {
@@ -213,7 +182,7 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     for (int k = 0; k < 8; ++k) {
         const int dir = order[k];
         if (!(path_mask & (1u << dir))) continue;
-        const long long lines = (long long)g.B * lines_per_stream(kDX[dir], kDY[dir], g.W, g.H);
+        const long long lines = (long long)g.B * lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H);
         plan.dir[plan.ndir] = dir;
         plan.plane_of[plan.ndir] = plane_index[dir];
         plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + (lines + lines_per_warp - 1) / lines_per_warp;

@@ -13,6 +13,54 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b)
 
 constexpr int kUpdWarps = 4;
 
+// S = sum of the direction planes over the cells [c0, c1), written to S and to
+// the warp's staging buffer (indexed from c0).  8-bit planes are read four
+// cells per 32-bit load (planes start 16-element aligned; the aligned words
+// around the span stay inside the plane allocation) and summed as two 16-bit
+// pairs, which cannot carry: 8 planes x 255 < 2^16.
+__device__ __forceinline__ void sum_planes(const uint8_t *__restrict__ planes, long long stride, int nplanes,
+                                           unsigned c0, unsigned c1, uint16_t *__restrict__ S,
+                                           uint16_t *stage, int lane)
+{
+    const unsigned a0 = c0 & ~3u;
+    const int nwords = (int)((c1 - a0 + 3) >> 2);
+    for (int wi = lane; wi < nwords; wi += 32) {
+        const unsigned cell = a0 + 4u * (unsigned)wi;
+        unsigned even = 0, odd = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < nplanes) {
+                const unsigned v = *(const unsigned *)(planes + q * stride + cell);
+                even += v & 0x00FF00FFu;
+                odd += (v >> 8) & 0x00FF00FFu;
+            }
+        }
+        const unsigned s[4] = {even & 0xFFFFu, odd & 0xFFFFu, even >> 16, odd >> 16};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned c = cell + j;
+            if (c >= c0 && c < c1) {
+                S[c] = (uint16_t)s[j];
+                stage[c - c0] = (uint16_t)s[j];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, long long stride, int nplanes,
+                                           unsigned c0, unsigned c1, uint16_t *__restrict__ S,
+                                           uint16_t *stage, int lane)
+{
+    for (unsigned c = c0 + lane; c < c1; c += 32) {
+        unsigned v = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nplanes) v += planes[q * stride + c];
+        S[c] = (uint16_t)v;
+        stage[c - c0] = (uint16_t)v;
+    }
+}
+
 // K5: one warp per 32 consecutive pixels.  Their cells are one contiguous
 // span of the ragged volume (offsets are a raster-order prefix sum), so the
 // warp first sums the direction planes cell by cell with coalesced loads,
@@ -47,15 +95,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     const unsigned span0 = __shfl_sync(0xffffffffu, m.x, 0);
     const int nvalid = (int)min(32LL, g.NPIX - gi0);
     const unsigned last_end = __shfl_sync(0xffffffffu, m.x + (unsigned)w, nvalid - 1);
-    const int span = (int)(last_end - span0);
     uint16_t *stage = sS + warp * 32 * g.D;
-    for (int c = lane; c < span; c += 32) {
-        const long long cell = (long long)span0 + c;
-        unsigned v = 0;
-        for (int q = 0; q < nplanes; ++q) v += planes[q * plane_stride + cell];
-        S[cell] = (uint16_t)v;
-        stage[c] = (uint16_t)v;
-    }
+    sum_planes(planes, plane_stride, nplanes, span0, last_end, S, stage, lane);
     __syncwarp();
     if (!valid) return;
     const uint16_t *s = stage + (m.x - span0);
