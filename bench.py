@@ -52,6 +52,23 @@ def parse():
     return ap.parse_args()
 
 
+def stream_seeds(rank: int, batch: int) -> list:
+    """Seeds of the B streams a rank processes: disjoint across ranks, so the
+    ranks shard independent streams (weak scaling, no data-path collective)."""
+    return [1000 + 1000 * rank + b for b in range(batch)]
+
+
+def reduce_over_ranks(x: float, op: str, world: int, device=None) -> float:
+    """max or sum of a scalar over ranks (identity when world == 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -118,13 +135,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ inputs
 
-def make_inputs(B, nframes, seed0, device):
+def make_inputs(seeds, nframes, device):
     import torch
     import synth
     Ls, Rs, Ms, Ts = [], [], [], []
     K = None
-    for b in range(B):
-        s = synth.kitti_like_sequence(seed0 + b, n_frames=max(100, nframes), width=W, height=H, f=F,
+    for seed in seeds:
+        s = synth.kitti_like_sequence(seed, n_frames=max(100, nframes), width=W, height=H, f=F,
                                       baseline=BASE, device=device, render_frames=nframes)
         Ls.append(s["left"])
         Rs.append(s["right"])
@@ -211,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     B = args.batch
     nframes = 1 + args.warmup + args.steps
-    left, right, Rm, tv, K = make_inputs(B, nframes, 1000 + 1000 * rank, dev)
+    left, right, Rm, tv, K = make_inputs(stream_seeds(rank, B), nframes, dev)
     stream = torch.cuda.Stream(dev)
     P = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=B)
     gs = rs.Stream(P, stream)
@@ -221,18 +238,10 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", world, dev)
 
     def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(x, "sum", world, dev)
 
     def run(h, frames, host=None, out=None):
         for k in frames:
