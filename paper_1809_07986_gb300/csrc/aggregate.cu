@@ -6,13 +6,8 @@
 // of a path.  Each enabled direction writes its own plane of L_r; the update
 // kernel sums the planes into S.
 //
-// All enabled directions run in one launch.  A warp walks 32/G path lines at
-// once, G lanes per line (G = 8, 16 or 32, chosen from the window width):
-// the cells of the current pixel's window are spread over the G lanes (wider
-// windows loop in chunks of G), the predecessor's losses sit in a per-line
-// shared buffer indexed by absolute disparity, and m comes from a segmented
-// xor-shuffle reduction.  The pixel metadata (first cell, window) and the
-// first chunk of costs are fetched ahead.
+// All enabled directions run in one launch; a warp walks 32/G path lines, G
+// lanes per line for the common window width (see sweep below).
 #include "rsgm_internal.cuh"
 
 namespace rsgm {
@@ -52,63 +47,106 @@ __host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, 
     return dy == 0 ? H : (dx == 0 ? W : W + H - 1);
 }
 
-// Walks the 32/G lines line0 .. line0 + 32/G - 1 of direction (dx, dy).  The
-// direction is a run-time value so that one copy of this code serves all
-// eight (a per-direction copy overflows the instruction cache).  Metadata is
-// fetched two pixels ahead and the first chunk of costs one pixel ahead.
-template <int G, typename T>
-__device__ __forceinline__ void sweep(int dx, int dy, long long line0, const uint8_t *__restrict__ cost,
-                                      T *__restrict__ plane, const uint2 *__restrict__ meta,
-                                      const Geometry &g, int P1, int P2, uint16_t *wbuf)
+// Walks NS = 32 / G path lines of direction (dx, dy) with one warp.
+//
+// Narrow pixels (window width <= G) are handled by a segment of G lanes, one
+// cell per lane, and the segment's minimum comes from one reduction over the
+// segment's lane mask.  Wide pixels (the full-range windows of discontinuity
+// resets and pixels without a prediction) are handled afterwards by the whole
+// warp, one pixel at a time, 32 cells per pass.  The predecessor's losses sit
+// in a per-line shared buffer indexed by absolute disparity.  The direction is
+// a run-time value so that one copy of this code serves all eight (a copy per
+// direction overflows the instruction cache).  Metadata is fetched two pixels
+// ahead and the narrow pixels' costs one pixel ahead.
+template <typename T>
+__device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long line0,
+                                      const uint8_t *__restrict__ cost, T *__restrict__ plane,
+                                      const uint2 *__restrict__ meta, const Geometry &g, int P1, int P2,
+                                      uint16_t *wbuf)
 {
-    const int lane = threadIdx.x & 31, seg = lane / G, sl = lane - seg * G;
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / G;  // == NS for the idle lanes above NS * G
+    const int sl = lane - seg * G;
+    const unsigned low = G == 32 ? kFull : (1u << G) - 1u;
+    const unsigned segmask = seg < NS ? low << (seg * G) : ~((NS * G == 32) ? kFull : (1u << (NS * G)) - 1u);
     const int nl = lines_per_stream(dx, dy, g.W, g.H);
     const long long line = line0 + seg;
     int n = 0;
     const uint2 *mp = meta;
-    if (line < (long long)g.B * nl) {
+    if (seg < NS && line < (long long)g.B * nl) {
         const int b = (int)(line / nl);
         const int j = (int)(line - (long long)b * nl);
         int x, y;
         line_start(dx, dy, j, g.W, g.H, x, y, n);
         mp = meta + (long long)b * g.HW + (long long)y * g.W + x;
     }
-    int nmax = n;
-#pragma unroll
-    for (int o = G; o < 32; o <<= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+    const int nmax = (int)__reduce_max_sync(kFull, (unsigned)n);
     const int step = dy * g.W + dx;
-    uint16_t *bufA = wbuf + seg * 2 * g.D;
+    uint16_t *bufA = wbuf + min(seg, NS - 1) * 2 * g.D;
     uint16_t *bufB = bufA + g.D;
 
     uint2 mc = n > 0 ? mp[0] : make_uint2(0u, 0u);
     uint2 mn = n > 1 ? mp[step] : make_uint2(0u, 0u);
-    int c0 = (n > 0 && sl < (int)(mc.y >> 16)) ? (int)cost[mc.x + sl] : 0;
+    int c0 = (n > 0 && sl < (int)(mc.y >> 16) && (int)(mc.y >> 16) <= G) ? (int)cost[mc.x + sl] : 0;
     int plo = 0, pw = 0, pmin = 0;
     for (int i = 0; i < nmax; ++i) {
         mp += step;
         const uint2 mnn = (i + 2 < n) ? mp[step] : make_uint2(0u, 0u);
-        const int cn = (i + 1 < n && sl < (int)(mn.y >> 16)) ? (int)cost[mn.x + sl] : 0;
+        const int wn = (int)(mn.y >> 16);
+        const int cn = (i + 1 < n && sl < wn && wn <= G) ? (int)cost[mn.x + sl] : 0;
         const unsigned o = mc.x;
         const int lo = (int)(mc.y & 0xFFFFu);
         const int w = i < n ? (int)(mc.y >> 16) : 0;
-        uint16_t *cur = (i & 1) ? bufB : bufA;
-        const uint16_t *prv = (i & 1) ? bufA : bufB;
+        const int sel = i & 1;
         const int cap = i == 0 ? 0 : pmin + P2;
-        unsigned lmin = 0xFFFFu;
-        for (int k = sl; k < w; k += G) {
-            const int d = lo + k;
-            const int c = (k == sl) ? c0 : (int)cost[o + k];
+
+        // narrow pixels: one cell per lane of the line's segment
+        unsigned L = kInf;
+        if (w <= G && sl < w) {
+            const int d = lo + sl;
+            const uint16_t *prv = sel ? bufA : bufB;
             const int r = d - plo;
             const int p0v = (unsigned)r < (unsigned)pw ? (int)prv[d] : kInf;
             const int pmv = (unsigned)(r - 1) < (unsigned)pw ? (int)prv[d - 1] : kInf;
             const int ppv = (unsigned)(r + 1) < (unsigned)pw ? (int)prv[d + 1] : kInf;
-            const int L = c + min(min(p0v, cap), min(pmv, ppv) + P1) - pmin;
-            cur[d] = (uint16_t)L;
-            plane[o + k] = (T)L;
-            lmin = min(lmin, (unsigned)L);
+            const int Lv = c0 + min(min(p0v, cap), min(pmv, ppv) + P1) - pmin;
+            (sel ? bufB : bufA)[d] = (uint16_t)Lv;
+            plane[o + sl] = (T)Lv;
+            L = (unsigned)Lv;
         }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
+        unsigned lmin = __reduce_min_sync(segmask, L);
+
+        // wide pixels: the whole warp, one pixel at a time
+        unsigned wide = __ballot_sync(kFull, seg < NS && sl == 0 && w > G);
+        while (wide) {
+            const int src = __ffs(wide) - 1;
+            wide &= wide - 1;
+            const int s2 = src / G;
+            const unsigned f1 = __shfl_sync(kFull, (unsigned)lo | ((unsigned)plo << 16), src);
+            const unsigned f2 = __shfl_sync(kFull, (unsigned)w | ((unsigned)pw << 16), src);
+            const int pmin2 = __shfl_sync(kFull, pmin, src);
+            const unsigned o2 = __shfl_sync(kFull, o, src);
+            const int lo2 = (int)(f1 & 0xFFFFu), plo2 = (int)(f1 >> 16);
+            const int w2 = (int)(f2 & 0xFFFFu), pw2 = (int)(f2 >> 16);
+            const int cap2 = i == 0 ? 0 : pmin2 + P2;
+            uint16_t *b2 = wbuf + s2 * 2 * g.D;
+            uint16_t *cur2 = b2 + sel * g.D;
+            const uint16_t *prv2 = b2 + (sel ^ 1) * g.D;
+            unsigned m2 = kInf;
+            for (int k = lane; k < w2; k += 32) {
+                const int d = lo2 + k;
+                const int r = d - plo2;
+                const int p0v = (unsigned)r < (unsigned)pw2 ? (int)prv2[d] : kInf;
+                const int pmv = (unsigned)(r - 1) < (unsigned)pw2 ? (int)prv2[d - 1] : kInf;
+                const int ppv = (unsigned)(r + 1) < (unsigned)pw2 ? (int)prv2[d + 1] : kInf;
+                const int Lv = (int)cost[o2 + k] + min(min(p0v, cap2), min(pmv, ppv) + P1) - pmin2;
+                cur2[d] = (uint16_t)Lv;
+                plane[o2 + k] = (T)Lv;
+                m2 = min(m2, (unsigned)Lv);
+            }
+            m2 = __reduce_min_sync(kFull, m2);
+            if (seg == s2) lmin = m2;
+        }
         __syncwarp();
         pmin = (int)lmin;
         plo = lo;
@@ -123,7 +161,7 @@ __device__ __forceinline__ void sweep(int dx, int dy, long long line0, const uin
 __constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 __constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
-template <int G, typename T>
+template <typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_paths(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
             const __grid_constant__ PathPlan plan)
@@ -134,22 +172,26 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     if (gw >= plan.warp_begin[plan.ndir]) return;  // uniform per warp
     int s = 0;
     while (s + 1 < plan.ndir && gw >= plan.warp_begin[s + 1]) ++s;
-    const long long line0 = (gw - plan.warp_begin[s]) * (32 / G);
-    uint16_t *wbuf = smem + warp * (32 / G) * 2 * plan.g.D;
+    const long long line0 = (gw - plan.warp_begin[s]) * plan.lines_per_warp;
+    uint16_t *wbuf = smem + warp * plan.lines_per_warp * 2 * plan.g.D;
     T *plane = planes + (long long)plan.plane_of[s] * plan.plane_stride;
     const int dir = plan.dir[s];
-    sweep<G, T>(kDX[dir], kDY[dir], line0, cost, plane, meta, plan.g, plan.P1, plan.P2, wbuf);
+    sweep<T>(kDX[dir], kDY[dir], plan.lanes, plan.lines_per_warp, line0, cost, plane, meta, plan.g, plan.P1,
+             plan.P2, wbuf);
 }
 
-
-template <int G, typename T>
-cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
+template <typename T>
+cudaError_t launch_t(const Buffers &b, const PathPlan &plan, cudaStream_t st)
 {
     const long long warps = plan.warp_begin[plan.ndir];
     if (warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    const size_t smem = (size_t)kWarpsPerBlock * (32 / G) * 2 * plan.g.D * sizeof(uint16_t);
-    k_paths<G, T><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
+    const size_t smem = (size_t)kWarpsPerBlock * plan.lines_per_warp * 2 * plan.g.D * sizeof(uint16_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_paths<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_paths<T><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
     return cudaGetLastError();
 }
 
@@ -158,9 +200,11 @@ cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
 const int kHostDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 const int kHostDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
-int lanes_per_line(int widest_narrow_window)
+int lanes_per_line(int window)
 {
-    return widest_narrow_window <= 8 ? 8 : (widest_narrow_window <= 16 ? 16 : 32);
+    // One lane per cell of the common (predicted) window, at least 2 (at
+    // most 16 lines per warp); wider windows go through the whole-warp path.
+    return window < 2 ? 2 : (window > 32 ? 32 : window);
 }
 
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
@@ -178,7 +222,9 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     for (int i = 0; i < 8; ++i) plane_index[i] = (path_mask & (1u << i)) ? np++ : -1;
     plan.ndir = 0;
     plan.warp_begin[0] = 0;
-    const int lines_per_warp = 32 / lanes;
+    plan.lanes = lanes;
+    plan.lines_per_warp = 32 / lanes;
+    const int lines_per_warp = plan.lines_per_warp;
     for (int k = 0; k < 8; ++k) {
         const int dir = order[k];
         if (!(path_mask & (1u << dir))) continue;
@@ -188,14 +234,7 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
         plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + (lines + lines_per_warp - 1) / lines_per_warp;
         plan.ndir++;
     }
-    if (plane_bytes == 1) {
-        if (lanes == 8) return launch_g<8, uint8_t>(b, plan, st);
-        if (lanes == 16) return launch_g<16, uint8_t>(b, plan, st);
-        return launch_g<32, uint8_t>(b, plan, st);
-    }
-    if (lanes == 8) return launch_g<8, uint16_t>(b, plan, st);
-    if (lanes == 16) return launch_g<16, uint16_t>(b, plan, st);
-    return launch_g<32, uint16_t>(b, plan, st);
+    return plane_bytes == 1 ? launch_t<uint8_t>(b, plan, st) : launch_t<uint16_t>(b, plan, st);
 }
 
 }  // namespace rsgm

@@ -37,6 +37,8 @@ struct SplatArgs {
 struct PathPlan {
     Geometry g;
     int P1, P2;
+    int lanes;           // lanes per line for narrow pixels (the common window width)
+    int lines_per_warp;  // 32 / lanes
     int ndir;
     int dir[8];
     int plane_of[8];
