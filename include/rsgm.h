@@ -185,6 +185,34 @@ int rsgm_enable_stage_timing(rsgm_stream s, int enable);
  * number of frames to *frames, then starts a new accumulation. */
 int rsgm_stage_times(rsgm_stream s, double *ms, int32_t *frames);
 
+/*
+ * Offsets of a ragged cell volume without allocating device memory.  The
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc (for example a host application that allots all device memory
+ * up front, or code running where a device allocation would synchronise the
+ * device or be refused).
+ *
+ * windows: device, rows*width uint32 in the RSGM_BUF_WINDOW format
+ * (lo | width << 16, raster order).  offsets: device, rows*width uint32,
+ * receives the exclusive prefix sum of the widths in raster order (the
+ * RSGM_BUF_OFFSET layout of a handle whose B*H rows are `rows`).  total:
+ * device uint32 receiving the sum of all widths, or NULL.  The sum must stay
+ * below 2^32.  Work is enqueued on cuda_stream (cudaStream_t, NULL = legacy
+ * default stream); nothing is allocated.
+ *
+ * Scratch: a fixed 512 KiB array of device memory inside the library (row
+ * totals and row bases for up to 65536 rows), held on every GPU that loads
+ * the library until the process exits.  rows > 65536 is rejected with
+ * RSGM_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  Every call shares the one array: calls that overlap
+ * on the GPU (different streams, no ordering between them) race and give
+ * wrong offsets.  Each call writes every scratch entry it reads, so no
+ * clearing is needed between calls.
+ */
+int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t rows,
+                                uint32_t *offsets, uint32_t *total, void *cuda_stream);
+
 /* Waits for the handle's enqueued work; reports deferred device errors. */
 int rsgm_sync(rsgm_stream s);
 

@@ -81,6 +81,7 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_uint64)]),
     "rsgm_enable_stage_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "rsgm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    "rsgm_window_offsets_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "rsgm_sync": (ctypes.c_int, [_P]),
     "rsgm_destroy_stream": (ctypes.c_int, [_P]),
     "rsgm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -222,6 +223,15 @@ def rsgm_stage_times(h: int):
     n = ctypes.c_int32()
     _check(lib().rsgm_stage_times(h, ms, ctypes.byref(n)), "rsgm_stage_times")
     return dict(zip(STAGE_NAMES, list(ms))), n.value
+
+
+def rsgm_window_offsets_noalloc(windows, width: int, rows: int, offsets, total=None, cuda_stream=None):
+    """Ragged offsets of `windows` into `offsets` (device tensors) without any
+    device allocation; see include/rsgm.h."""
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    _check(lib().rsgm_window_offsets_noalloc(_ptr(windows), width, rows, _ptr(offsets), _ptr(total),
+                                             cuda_stream), "rsgm_window_offsets_noalloc")
 
 
 def rsgm_sync(h: int):

@@ -223,6 +223,11 @@ void destroy_timer(StageTimer &t)
 
 }  // namespace
 
+namespace rsgm {
+// Records `msg` as the calling thread's last error and returns `code`.
+int record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace rsgm
+
 extern "C" {
 
 int rsgm_default_params(rsgm_params *p, int32_t width, int32_t height)
