@@ -12,35 +12,40 @@ constexpr int kMaxHalf = 7;  // census_w, census_h <= 15
 // K2: one 32 x 8 tile of one image per block, staged in shared memory with a
 // clamped halo (pixels outside the image repeat the border).  Bit k of the
 // code is set iff the k-th window pixel in row-major order (centre skipped)
-// is darker than the centre.  blockIdx.z = 2 * stream + side.
+// is darker than the centre.  blockIdx.z = 2 * stream + side.  HW, HH > 0 fix
+// the half-window at compile time (the 5 x 5 of Table 1); 0 reads hw, hh.
+template <int HW, int HH>
 __global__ void __launch_bounds__(kTileX *kTileY) k_census(const uint8_t *__restrict__ left,
                                                            const uint8_t *__restrict__ right,
                                                            unsigned long long *__restrict__ cen_l,
                                                            unsigned long long *__restrict__ cen_r,
-                                                           Geometry g, int hw, int hh)
+                                                           Geometry g, int hw_rt, int hh_rt)
 {
     __shared__ uint8_t tile[kTileY + 2 * kMaxHalf][kTileX + 2 * kMaxHalf];
-    int b = blockIdx.z >> 1, side = blockIdx.z & 1;
+    const int hw = HW > 0 ? HW : hw_rt, hh = HH > 0 ? HH : hh_rt;
+    const int b = blockIdx.z >> 1, side = blockIdx.z & 1;
     const uint8_t *img = (side ? right : left) + (long long)b * g.HW;
     unsigned long long *out = (side ? cen_r : cen_l) + (long long)b * g.HW;
-    int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-    int tw = kTileX + 2 * hw, th = kTileY + 2 * hh;
-    int tid = threadIdx.y * kTileX + threadIdx.x;
-    for (int i = tid; i < tw * th; i += kTileX * kTileY) {
-        int ty = i / tw, tx = i - ty * tw;
-        int gx = min(max(x0 - hw + tx, 0), g.W - 1);
-        int gy = min(max(y0 - hh + ty, 0), g.H - 1);
-        tile[ty][tx] = img[(long long)gy * g.W + gx];
+    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+    const int tw = kTileX + 2 * hw, th = kTileY + 2 * hh;
+    for (int ty = threadIdx.y; ty < th; ty += kTileY) {
+        const int gy = min(max(y0 - hh + ty, 0), g.H - 1);
+        const uint8_t *row = img + (long long)gy * g.W;
+        for (int tx = threadIdx.x; tx < tw; tx += kTileX) tile[ty][tx] = row[min(max(x0 - hw + tx, 0), g.W - 1)];
     }
     __syncthreads();
-    int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= g.W || y >= g.H) return;
-    int cx = threadIdx.x + hw, cy = threadIdx.y + hh;
-    uint8_t c = tile[cy][cx];
+    const int cx = threadIdx.x + hw, cy = threadIdx.y + hh;
+    const uint8_t c = tile[cy][cx];
     unsigned long long code = 0;
     int bit = 0;
-    for (int dy = -hh; dy <= hh; ++dy) {
-        for (int dx = -hw; dx <= hw; ++dx) {
+#pragma unroll
+    for (int dy = -(HH > 0 ? HH : kMaxHalf); dy <= (HH > 0 ? HH : kMaxHalf); ++dy) {
+        if (HH == 0 && (dy < -hh || dy > hh)) continue;
+#pragma unroll
+        for (int dx = -(HW > 0 ? HW : kMaxHalf); dx <= (HW > 0 ? HW : kMaxHalf); ++dx) {
+            if (HW == 0 && (dx < -hw || dx > hw)) continue;
             if (dx == 0 && dy == 0) continue;
             if (tile[cy + dy][cx + dx] < c) code |= 1ull << bit;
             ++bit;
@@ -49,30 +54,61 @@ __global__ void __launch_bounds__(kTileX *kTileY) k_census(const uint8_t *__rest
     out[(long long)y * g.W + x] = code;
 }
 
-// K3: one thread per pixel.  Finalises the pixel's metadata (first cell =
-// row base + in-row prefix, window) and writes C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)) for its
-// window; a match left of the image costs every census bit.
-__global__ void __launch_bounds__(256) k_cost(const unsigned long long *__restrict__ cen_l,
-                                              const unsigned long long *__restrict__ cen_r,
-                                              const uint32_t *__restrict__ win,
-                                              const uint32_t *__restrict__ inrow,
-                                              const uint32_t *__restrict__ row_base,
-                                              uint2 *__restrict__ meta, uint8_t *__restrict__ cost,
-                                              Geometry g, int nbits)
+constexpr int kCostWarps = 4;
+
+// K3: one warp per 32 consecutive pixels.  Each lane finalises one pixel's
+// metadata (first cell = row base + in-row prefix, window); the pixels' cells
+// form one contiguous span (raster-order prefix sum), which the warp then
+// walks 32 cells at a time: a lane finds its cell's pixel by a binary search
+// over the lanes' first cells and writes C(p, d) = popcount(cL(x,y) ^
+// cR(x-d,y)); a match left of the image costs every census bit.
+__global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long long *__restrict__ cen_l,
+                                                         const unsigned long long *__restrict__ cen_r,
+                                                         const uint32_t *__restrict__ win,
+                                                         const uint32_t *__restrict__ inrow,
+                                                         const uint32_t *__restrict__ row_base,
+                                                         uint2 *__restrict__ meta, uint8_t *__restrict__ cost,
+                                                         Geometry g, int nbits)
 {
-    long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= g.NPIX) return;
-    long long row = gi / g.W;
-    int x = (int)(gi - row * g.W);
-    uint32_t o = row_base[row] + inrow[gi];
-    uint32_t wv = win[gi];
-    meta[gi] = make_uint2(o, wv);
-    int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
-    unsigned long long cl = cen_l[gi];
-    const unsigned long long *rr = cen_r + row * g.W;
-    for (int k = 0; k < w; ++k) {
-        int xr = x - (lo + k);
-        cost[o + k] = (uint8_t)(xr >= 0 ? __popcll(cl ^ rr[xr]) : nbits);
+    const int lane = threadIdx.x & 31;
+    const long long gi0 = ((long long)blockIdx.x * kCostWarps + (threadIdx.x >> 5)) * 32;
+    if (gi0 >= g.NPIX) return;  // uniform per warp
+    const int nvalid = (int)min(32LL, g.NPIX - gi0);
+    const long long gi = gi0 + lane;
+    unsigned o = 0, wv = 0;
+    int x = 0;
+    long long row = 0;
+    unsigned long long cl = 0;
+    if (lane < nvalid) {
+        row = gi / g.W;
+        x = (int)(gi - row * g.W);
+        o = row_base[row] + inrow[gi];
+        wv = win[gi];
+        meta[gi] = make_uint2(o, wv);
+        cl = cen_l[gi];
+    }
+    const unsigned span0 = __shfl_sync(0xffffffffu, o, 0);
+    const unsigned span1 = __shfl_sync(0xffffffffu, o + (wv >> 16), nvalid - 1);
+    for (unsigned base = span0; base < span1; base += 32) {  // uniform trip count: shuffles inside
+        const unsigned c = base + lane;
+        // pixel of cell c: the last lane whose first cell is <= c
+        int j = 0;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const int t = j + s;
+            const unsigned ot = __shfl_sync(0xffffffffu, o, t & 31);
+            if (t < nvalid && ot <= c) j = t;
+        }
+        const unsigned oj = __shfl_sync(0xffffffffu, o, j);
+        const unsigned wj = __shfl_sync(0xffffffffu, wv, j);
+        const int xj = __shfl_sync(0xffffffffu, x, j);
+        const long long rj = __shfl_sync(0xffffffffu, row, j);
+        const unsigned long long clj = __shfl_sync(0xffffffffu, cl, j);
+        if (c < span1) {
+            const int d = (int)(wj & 0xFFFFu) + (int)(c - oj);
+            const int xr = xj - d;
+            cost[c] = (uint8_t)(xr >= 0 ? __popcll(clj ^ cen_r[rj * g.W + xr]) : nbits);
+        }
     }
 }
 
@@ -82,14 +118,18 @@ cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *le
                           const uint8_t *right, int cw, int ch, cudaStream_t st)
 {
     dim3 grid((g.W + kTileX - 1) / kTileX, (g.H + kTileY - 1) / kTileY, 2 * g.B);
-    k_census<<<grid, dim3(kTileX, kTileY), 0, st>>>(left, right, b.cen_l, b.cen_r, g, cw / 2, ch / 2);
+    if (cw == 5 && ch == 5)
+        k_census<2, 2><<<grid, dim3(kTileX, kTileY), 0, st>>>(left, right, b.cen_l, b.cen_r, g, 2, 2);
+    else
+        k_census<0, 0><<<grid, dim3(kTileX, kTileY), 0, st>>>(left, right, b.cen_l, b.cen_r, g, cw / 2, ch / 2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStream_t st)
 {
-    unsigned blocks = (unsigned)((g.NPIX + 255) / 256);
-    k_cost<<<blocks, 256, 0, st>>>(b.cen_l, b.cen_r, b.win, b.inrow, b.row_base, b.meta, b.cost, g, nbits);
+    const long long warps = (g.NPIX + 31) / 32;
+    const unsigned blocks = (unsigned)((warps + kCostWarps - 1) / kCostWarps);
+    k_cost<<<blocks, kCostWarps * 32, 0, st>>>(b.cen_l, b.cen_r, b.win, b.inrow, b.row_base, b.meta, b.cost, g, nbits);
     return cudaGetLastError();
 }
 

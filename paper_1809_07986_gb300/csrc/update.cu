@@ -22,26 +22,40 @@ __device__ __forceinline__ void sum_planes(const uint8_t *__restrict__ planes, l
                                            unsigned c0, unsigned c1, uint16_t *__restrict__ S,
                                            uint16_t *stage, int lane)
 {
+    constexpr int kWordsPerLane = 4;  // all loads of a batch are issued before any is used
     const unsigned a0 = c0 & ~3u;
     const int nwords = (int)((c1 - a0 + 3) >> 2);
-    for (int wi = lane; wi < nwords; wi += 32) {
-        const unsigned cell = a0 + 4u * (unsigned)wi;
-        unsigned even = 0, odd = 0;
+    for (int base = 0; base < nwords; base += 32 * kWordsPerLane) {
+        unsigned even[kWordsPerLane], odd[kWordsPerLane];
+#pragma unroll
+        for (int u = 0; u < kWordsPerLane; ++u) even[u] = odd[u] = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             if (q < nplanes) {
-                const unsigned v = *(const unsigned *)(planes + q * stride + cell);
-                even += v & 0x00FF00FFu;
-                odd += (v >> 8) & 0x00FF00FFu;
+#pragma unroll
+                for (int u = 0; u < kWordsPerLane; ++u) {
+                    const int wi = base + u * 32 + lane;
+                    if (wi < nwords) {
+                        const unsigned v = *(const unsigned *)(planes + q * stride + a0 + 4u * (unsigned)wi);
+                        even[u] += v & 0x00FF00FFu;
+                        odd[u] += (v >> 8) & 0x00FF00FFu;
+                    }
+                }
             }
         }
-        const unsigned s[4] = {even & 0xFFFFu, odd & 0xFFFFu, even >> 16, odd >> 16};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const unsigned c = cell + j;
-            if (c >= c0 && c < c1) {
-                S[c] = (uint16_t)s[j];
-                stage[c - c0] = (uint16_t)s[j];
+        for (int u = 0; u < kWordsPerLane; ++u) {
+            const int wi = base + u * 32 + lane;
+            if (wi >= nwords) continue;
+            const unsigned cell = a0 + 4u * (unsigned)wi;
+            const unsigned s[4] = {even[u] & 0xFFFFu, odd[u] & 0xFFFFu, even[u] >> 16, odd[u] >> 16};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned c = cell + j;
+                if (c >= c0 && c < c1) {
+                    S[c] = (uint16_t)s[j];
+                    stage[c - c0] = (uint16_t)s[j];
+                }
             }
         }
     }
