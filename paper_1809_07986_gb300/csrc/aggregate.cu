@@ -47,17 +47,54 @@ __host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, 
     return dy == 0 ? H : (dx == 0 ? W : W + H - 1);
 }
 
+constexpr int kV = 3;   // cells per lane for narrow pixels
+constexpr int kVW = 4;  // cells per lane for wide pixels
+constexpr int kPad = 6; // uint16 padding between the lines' buffers: 3 banks apart
+
+// uint16 elements of shared memory per line: two buffers of D losses + padding.
+__host__ __device__ __forceinline__ int line_stride(int D) { return 2 * D + kPad; }
+
+// Eq. 1 for kN consecutive cells d0 .. d0+kN-1 of one pixel (cells k0 + v of
+// its window, up to w): the predecessor's losses at d0-1 .. d0+kN come from
+// its buffer `prv` (+inf outside [plo, plo + pw)); cap = m + P2 (0 on the
+// first pixel of a path), sub = m.  Writes the losses to `cur` and the plane,
+// returns their minimum.
+template <int kN, typename T>
+__device__ __forceinline__ unsigned cells(const uint8_t *cst, T *pl, const uint16_t *prv, uint16_t *cur,
+                                          int d0, int k0, int w, int plo, int pw, int cap, int sub, int P1)
+{
+    int pv[kN + 2];
+#pragma unroll
+    for (int t = 0; t < kN + 2; ++t) {
+        const int dd = d0 - 1 + t;
+        pv[t] = (unsigned)(dd - plo) < (unsigned)pw ? (int)prv[dd] : kInf;
+    }
+    unsigned m = kInf;
+#pragma unroll
+    for (int v = 0; v < kN; ++v) {
+        if (k0 + v < w) {
+            const int L = (int)cst[v] + min(min(pv[v + 1], cap), min(pv[v], pv[v + 2]) + P1) - sub;
+            cur[d0 + v] = (uint16_t)L;
+            pl[v] = (T)L;
+            m = min(m, (unsigned)L);
+        }
+    }
+    return m;
+}
+
 // Walks NS = 32 / G path lines of direction (dx, dy) with one warp.
 //
-// Narrow pixels (window width <= G) are handled by a segment of G lanes, one
-// cell per lane, and the segment's minimum comes from one reduction over the
-// segment's lane mask.  Wide pixels (the full-range windows of discontinuity
-// resets and pixels without a prediction) are handled afterwards by the whole
-// warp, one pixel at a time, 32 cells per pass.  The predecessor's losses sit
-// in a per-line shared buffer indexed by absolute disparity.  The direction is
-// a run-time value so that one copy of this code serves all eight (a copy per
-// direction overflows the instruction cache).  Metadata is fetched two pixels
-// ahead and the narrow pixels' costs one pixel ahead.
+// Narrow pixels (window width <= G * kV) are handled by the line's segment of
+// G lanes, kV consecutive cells per lane; the segment's minimum comes from
+// one reduction over the segment's lane mask.  Wide pixels (the full-range
+// windows of discontinuity resets and pixels without a prediction) are
+// handled afterwards by the whole warp, one pixel at a time, kVW cells per
+// lane.  The predecessor's losses sit in a per-line shared buffer indexed by
+// absolute disparity.  The direction is a run-time value so that one copy of
+// this code serves all eight (a copy per direction overflows the instruction
+// cache).  Metadata is fetched two pixels ahead, narrow pixels' costs one
+// pixel ahead.  The lines' buffers are padded apart by three banks: adjacent
+// lines read similar disparities at the same time.
 template <typename T>
 __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long line0,
                                       const uint8_t *__restrict__ cost, T *__restrict__ plane,
@@ -67,6 +104,8 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
     const int lane = threadIdx.x & 31;
     const int seg = lane / G;  // == NS for the idle lanes above NS * G
     const int sl = lane - seg * G;
+    const int kb = sl * kV;    // first window cell of this lane (narrow pixels)
+    const int cap_n = G * kV;  // widest narrow window
     const unsigned low = G == 32 ? kFull : (1u << G) - 1u;
     const unsigned segmask = seg < NS ? low << (seg * G) : ~((NS * G == 32) ? kFull : (1u << (NS * G)) - 1u);
     const int nl = lines_per_stream(dx, dy, g.W, g.H);
@@ -82,42 +121,42 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
     }
     const int nmax = (int)__reduce_max_sync(kFull, (unsigned)n);
     const int step = dy * g.W + dx;
-    uint16_t *bufA = wbuf + min(seg, NS - 1) * 2 * g.D;
+    uint16_t *bufA = wbuf + min(seg, NS - 1) * line_stride(g.D);
     uint16_t *bufB = bufA + g.D;
 
     uint2 mc = n > 0 ? mp[0] : make_uint2(0u, 0u);
     uint2 mn = n > 1 ? mp[step] : make_uint2(0u, 0u);
-    int c0 = (n > 0 && sl < (int)(mc.y >> 16) && (int)(mc.y >> 16) <= G) ? (int)cost[mc.x + sl] : 0;
+    uint8_t cc[kV];
+    {
+        const int w0 = (int)(mc.y >> 16);
+#pragma unroll
+        for (int v = 0; v < kV; ++v) cc[v] = (n > 0 && kb + v < w0 && w0 <= cap_n) ? cost[mc.x + kb + v] : 0;
+    }
     int plo = 0, pw = 0, pmin = 0;
     for (int i = 0; i < nmax; ++i) {
         mp += step;
         const uint2 mnn = (i + 2 < n) ? mp[step] : make_uint2(0u, 0u);
-        const int wn = (int)(mn.y >> 16);
-        const int cn = (i + 1 < n && sl < wn && wn <= G) ? (int)cost[mn.x + sl] : 0;
+        uint8_t cn[kV];
+        {
+            const int wn = (int)(mn.y >> 16);
+#pragma unroll
+            for (int v = 0; v < kV; ++v)
+                cn[v] = (i + 1 < n && kb + v < wn && wn <= cap_n) ? cost[mn.x + kb + v] : 0;
+        }
         const unsigned o = mc.x;
         const int lo = (int)(mc.y & 0xFFFFu);
         const int w = i < n ? (int)(mc.y >> 16) : 0;
         const int sel = i & 1;
         const int cap = i == 0 ? 0 : pmin + P2;
 
-        // narrow pixels: one cell per lane of the line's segment
-        unsigned L = kInf;
-        if (w <= G && sl < w) {
-            const int d = lo + sl;
-            const uint16_t *prv = sel ? bufA : bufB;
-            const int r = d - plo;
-            const int p0v = (unsigned)r < (unsigned)pw ? (int)prv[d] : kInf;
-            const int pmv = (unsigned)(r - 1) < (unsigned)pw ? (int)prv[d - 1] : kInf;
-            const int ppv = (unsigned)(r + 1) < (unsigned)pw ? (int)prv[d + 1] : kInf;
-            const int Lv = c0 + min(min(p0v, cap), min(pmv, ppv) + P1) - pmin;
-            (sel ? bufB : bufA)[d] = (uint16_t)Lv;
-            plane[o + sl] = (T)Lv;
-            L = (unsigned)Lv;
-        }
-        unsigned lmin = __reduce_min_sync(segmask, L);
+        unsigned lmin = kInf;
+        if (w <= cap_n && kb < w)
+            lmin = cells<kV, T>(cc, plane + o + kb, sel ? bufA : bufB, sel ? bufB : bufA, lo + kb, kb, w, plo, pw,
+                                cap, pmin, P1);
+        lmin = __reduce_min_sync(segmask, lmin);
 
         // wide pixels: the whole warp, one pixel at a time
-        unsigned wide = __ballot_sync(kFull, seg < NS && sl == 0 && w > G);
+        unsigned wide = __ballot_sync(kFull, seg < NS && sl == 0 && w > cap_n);
         while (wide) {
             const int src = __ffs(wide) - 1;
             wide &= wide - 1;
@@ -129,20 +168,14 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
             const int lo2 = (int)(f1 & 0xFFFFu), plo2 = (int)(f1 >> 16);
             const int w2 = (int)(f2 & 0xFFFFu), pw2 = (int)(f2 >> 16);
             const int cap2 = i == 0 ? 0 : pmin2 + P2;
-            uint16_t *b2 = wbuf + s2 * 2 * g.D;
-            uint16_t *cur2 = b2 + sel * g.D;
-            const uint16_t *prv2 = b2 + (sel ^ 1) * g.D;
+            uint16_t *b2 = wbuf + s2 * line_stride(g.D);
             unsigned m2 = kInf;
-            for (int k = lane; k < w2; k += 32) {
-                const int d = lo2 + k;
-                const int r = d - plo2;
-                const int p0v = (unsigned)r < (unsigned)pw2 ? (int)prv2[d] : kInf;
-                const int pmv = (unsigned)(r - 1) < (unsigned)pw2 ? (int)prv2[d - 1] : kInf;
-                const int ppv = (unsigned)(r + 1) < (unsigned)pw2 ? (int)prv2[d + 1] : kInf;
-                const int Lv = (int)cost[o2 + k] + min(min(p0v, cap2), min(pmv, ppv) + P1) - pmin2;
-                cur2[d] = (uint16_t)Lv;
-                plane[o2 + k] = (T)Lv;
-                m2 = min(m2, (unsigned)Lv);
+            for (int k0 = lane * kVW; k0 < w2; k0 += 32 * kVW) {
+                uint8_t c4[kVW];
+#pragma unroll
+                for (int v = 0; v < kVW; ++v) c4[v] = k0 + v < w2 ? cost[o2 + k0 + v] : 0;
+                m2 = min(m2, cells<kVW, T>(c4, plane + o2 + k0, b2 + (sel ^ 1) * g.D, b2 + sel * g.D, lo2 + k0, k0,
+                                           w2, plo2, pw2, cap2, pmin2, P1));
             }
             m2 = __reduce_min_sync(kFull, m2);
             if (seg == s2) lmin = m2;
@@ -153,7 +186,8 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
         pw = w;
         mc = mn;
         mn = mnn;
-        c0 = cn;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) cc[v] = cn[v];
     }
 }
 
@@ -162,7 +196,7 @@ __constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 __constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_paths(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
             const __grid_constant__ PathPlan plan)
 {
@@ -173,7 +207,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     int s = 0;
     while (s + 1 < plan.ndir && gw >= plan.warp_begin[s + 1]) ++s;
     const long long line0 = (gw - plan.warp_begin[s]) * plan.lines_per_warp;
-    uint16_t *wbuf = smem + warp * plan.lines_per_warp * 2 * plan.g.D;
+    uint16_t *wbuf = smem + warp * plan.lines_per_warp * line_stride(plan.g.D);
     T *plane = planes + (long long)plan.plane_of[s] * plan.plane_stride;
     const int dir = plan.dir[s];
     sweep<T>(kDX[dir], kDY[dir], plan.lanes, plan.lines_per_warp, line0, cost, plane, meta, plan.g, plan.P1,
@@ -186,7 +220,7 @@ cudaError_t launch_t(const Buffers &b, const PathPlan &plan, cudaStream_t st)
     const long long warps = plan.warp_begin[plan.ndir];
     if (warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    const size_t smem = (size_t)kWarpsPerBlock * plan.lines_per_warp * 2 * plan.g.D * sizeof(uint16_t);
+    const size_t smem = (size_t)kWarpsPerBlock * plan.lines_per_warp * line_stride(plan.g.D) * sizeof(uint16_t);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_paths<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -202,9 +236,11 @@ const int kHostDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
 int lanes_per_line(int window)
 {
-    // One lane per cell of the common (predicted) window, at least 2 (at
-    // most 16 lines per warp); wider windows go through the whole-warp path.
-    return window < 2 ? 2 : (window > 32 ? 32 : window);
+    // Enough lanes (3 cells each) for the common (predicted) window, at least
+    // 2 (at most 16 lines per warp); wider windows go through the whole-warp
+    // path.
+    const int G = (window + kV - 1) / kV;
+    return G < 2 ? 2 : (G > 32 ? 32 : G);
 }
 
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
