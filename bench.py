@@ -42,7 +42,7 @@ NCU_TRAFFIC_BYTES_PER_LAUNCH = None
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=32, help="camera streams per GPU")
@@ -251,7 +251,8 @@ def run_ours(args, rank, world, local_rank):
                 rs.rsgm_reduced_frame(h, host[0][k], host[1][k], Rm[k], tv[k], K, BASE)
                 rs.rsgm_state(h, out[0], None, out[1], None)
 
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), ClockSampler(local_rank) as clk:
+        # the sampler runs from the warm-up on, so that it sees the GPU under load
         gs.full_frame(left[0], right[0])
         run(gs.handle, range(1, 1 + args.warmup))
         gs.sync()
@@ -259,11 +260,10 @@ def run_ours(args, rank, world, local_rank):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
-        with ClockSampler(local_rank) as clk:
-            ev0.record(stream)
-            run(gs.handle, range(1 + args.warmup, nframes))
-            ev1.record(stream)
-            torch.cuda.synchronize()
+        ev0.record(stream)
+        run(gs.handle, range(1 + args.warmup, nframes))
+        ev1.record(stream)
+        torch.cuda.synchronize()
         elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
         barrier()
         f1, c1, _ = gs.counters()
@@ -366,9 +366,16 @@ def run_ours(args, rank, world, local_rank):
                 evs[k - 1][1].record(stream)
             torch.cuda.synchronize()
         lat = sorted(a.elapsed_time(b) for a, b in evs[args.warmup:] or evs)
+        # where a single stream's frame spends its time
+        with torch.cuda.stream(stream):
+            rs.rsgm_enable_stage_timing(g1.handle, True)
+            for k in range(1, nframes):
+                rs.rsgm_reduced_frame(g1.handle, left[k, 0], right[k, 0], Rm[k, :1], tv[k, :1], K, BASE)
+            st1, n1 = rs.rsgm_stage_times(g1.handle)
         g1.close()
         q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
-        result["latency_ms"] = {"p50": q(0.5), "p99": q(0.99), "frames": len(lat), "streams": 1}
+        result["latency_ms"] = {"p50": q(0.5), "p99": q(0.99), "frames": len(lat), "streams": 1,
+                                "stage_ms": {k: v / max(n1, 1) for k, v in st1.items()}}
 
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)

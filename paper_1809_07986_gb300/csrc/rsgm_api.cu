@@ -294,7 +294,7 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc(&b.p_pred, n, all, nall)) || (rc = alloc(&b.win, n, all, nall)) ||
         (rc = alloc(&b.cls, n, all, nall)) || (rc = alloc(&b.inrow, n, all, nall)) ||
         (rc = alloc(&b.meta, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
-        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells, all, nall)) ||
+        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells + 16, all, nall)) ||  // + the aligned-word over-read of staged copies
         (rc = alloc((uint8_t **)&b.planes, (size_t)plane_stride(s->g) * s->nplanes * s->plane_bytes, all, nall)) ||
         (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
         (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
