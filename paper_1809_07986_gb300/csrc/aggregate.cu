@@ -72,12 +72,15 @@ __device__ __forceinline__ unsigned cells(const uint8_t *cst, T *pl, const uint1
     unsigned m = kInf;
 #pragma unroll
     for (int v = 0; v < kN; ++v) {
-        if (k0 + v < w) {
-            const int L = (int)cst[v] + min(min(pv[v + 1], cap), min(pv[v], pv[v + 2]) + P1) - sub;
+        // computed unconditionally; only the stores and the minimum are
+        // predicated, so the body has no branches
+        const int L = (int)cst[v] + min(min(pv[v + 1], cap), min(pv[v], pv[v + 2]) + P1) - sub;
+        const bool in = k0 + v < w;
+        if (in) {
             cur[d0 + v] = (uint16_t)L;
             pl[v] = (T)L;
-            m = min(m, (unsigned)L);
         }
+        m = in ? min(m, (unsigned)L) : m;
     }
     return m;
 }

@@ -12,6 +12,7 @@ __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 
 constexpr int kUpdWarps = 4;
+constexpr int kStageCells = 1024;  // per-warp staging of S; larger spans read S from global memory
 
 // S = sum of the direction planes over the cells [c0, c1), written to S and to
 // the warp's staging buffer (indexed from c0).  8-bit planes are read four
@@ -54,7 +55,7 @@ __device__ __forceinline__ void sum_planes(const uint8_t *__restrict__ planes, l
                 const unsigned c = cell + j;
                 if (c >= c0 && c < c1) {
                     S[c] = (uint16_t)s[j];
-                    stage[c - c0] = (uint16_t)s[j];
+                    if (stage) stage[c - c0] = (uint16_t)s[j];
                 }
             }
         }
@@ -71,15 +72,15 @@ __device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, 
         for (int q = 0; q < 8; ++q)
             if (q < nplanes) v += planes[q * stride + c];
         S[c] = (uint16_t)v;
-        stage[c - c0] = (uint16_t)v;
+        if (stage) stage[c - c0] = (uint16_t)v;
     }
 }
 
 // K5: one warp per 32 consecutive pixels.  Their cells are one contiguous
 // span of the ragged volume (offsets are a raster-order prefix sum), so the
 // warp first sums the direction planes cell by cell with coalesced loads,
-// S(p,d) = sum_r L_r(p,d) (Section 2.2), writes S and stages it in shared
-// memory; then each lane takes one pixel: d_int = first minimum of S over the
+// S(p,d) = sum_r L_r(p,d) (Section 2.2), writes S and, for spans of up to
+// kStageCells cells, stages it in shared memory; then each lane takes one pixel: d_int = first minimum of S over the
 // window; with both neighbours inside the window and den = S- - 2 S0 + S+ > 0
 // the measurement is d_int + (S- - S+) / (2 den).  Pixels without a
 // prediction take the measurement (d = d_z, p = r).  Otherwise
@@ -109,11 +110,12 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     const unsigned span0 = __shfl_sync(0xffffffffu, m.x, 0);
     const int nvalid = (int)min(32LL, g.NPIX - gi0);
     const unsigned last_end = __shfl_sync(0xffffffffu, m.x + (unsigned)w, nvalid - 1);
-    uint16_t *stage = sS + warp * 32 * g.D;
+    const bool staged = last_end - span0 <= (unsigned)kStageCells;
+    uint16_t *stage = staged ? sS + warp * kStageCells : nullptr;
     sum_planes(planes, plane_stride, nplanes, span0, last_end, S, stage, lane);
-    __syncwarp();
+    __syncwarp();  // S (shared or global) complete for the warp
     if (!valid) return;
-    const uint16_t *s = stage + (m.x - span0);
+    const uint16_t *s = staged ? stage + (m.x - span0) : S + m.x;
     int best = 0;
     unsigned bs = s[0];
     for (int k = 1; k < w; ++k) {
@@ -164,13 +166,7 @@ cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams
 {
     const unsigned blocks = (unsigned)((g.NPIX + kUpdWarps * 32 - 1) / (kUpdWarps * 32));
     const long long stride = plane_stride(g);
-    const size_t smem = (size_t)kUpdWarps * 32 * g.D * sizeof(uint16_t);
-    if (smem > 48 * 1024) {  // D > 192: opt in to the larger shared-memory carve-out
-        cudaError_t e = plane_bytes == 1
-            ? cudaFuncSetAttribute(k_update<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-            : cudaFuncSetAttribute(k_update<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const size_t smem = (size_t)kUpdWarps * kStageCells * sizeof(uint16_t);
     if (plane_bytes == 1)
         k_update<uint8_t><<<blocks, kUpdWarps * 32, smem, st>>>((const uint8_t *)b.planes, stride, nplanes, b.S, b.meta,
                                                   b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
