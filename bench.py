@@ -34,9 +34,12 @@ METRIC = "frames/s and cost-cell updates/s at 1242x375 vs plain form; p99 latenc
 # direction): + C, two + P1, three min (d, d-1, d+1 against m + P2), - m, the
 # running minimum for the next pixel, + into S.
 OPS_PER_CELL_PATH = 9
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from the committed ncu capture (None until one matches the kernel).
-NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of the
+# dominant kernel, from the ncu capture in profiles/k_paths_kitti_b8.md
+# (8 streams: 665.2 MB for 51.7 M cells); the 32-stream launch is too large
+# to capture, and its traffic is this figure times its cells.  None once the
+# kernel changes without a new capture.
+NCU_DRAM_BYTES_PER_CELL = 12.86
 
 
 def parse():
@@ -306,7 +309,9 @@ def run_ours(args, rank, world, local_rank):
     result["stage_ms_per_step"] = {k: v / max(st_frames, 1) for k, v in st_ms.items()}
     result["roofline"] = {"kernel": "k_paths (all 8 directions, one launch)", "bound": "alu", "achieved": achieved_tops,
                           "peak": int_peak_tops, "unit": "Tops/s", "frac": achieved_tops / int_peak_tops,
-                          "traffic": NCU_TRAFFIC_BYTES_PER_LAUNCH,
+                          "traffic": (NCU_DRAM_BYTES_PER_CELL * cells_per_frame
+                                      if NCU_DRAM_BYTES_PER_CELL else None),
+                          "traffic_unit": "bytes per launch (ncu, scaled by cells from 8 streams)",
                           "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_max,
                           "ops_per_cell_path": OPS_PER_CELL_PATH,
                           "share_of_step": agg_ms / total_ms if total_ms else None}

@@ -247,7 +247,7 @@ int lanes_per_line(int window)
 }
 
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         int lanes, int plane_bytes, cudaStream_t st)
+                         int lanes, int plane_bytes, int sm_count, cudaStream_t st)
 {
     PathPlan plan;
     plan.g = g;
@@ -262,7 +262,15 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     plan.ndir = 0;
     plan.warp_begin[0] = 0;
     plan.lanes = lanes;
-    plan.lines_per_warp = 32 / lanes;
+    // Lines per warp: as many as the lanes allow (32 / lanes), fewer when the
+    // batch is small, so that the launch still fills every SM with 32 warps;
+    // a warp's steps run one after another, so small batches favour more,
+    // shorter-running warps.
+    long long total_lines = 0;
+    for (int dir = 0; dir < 8; ++dir)
+        if (path_mask & (1u << dir)) total_lines += (long long)g.B * lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H);
+    const long long fill = total_lines / ((long long)(sm_count > 0 ? sm_count : 152) * 32);
+    plan.lines_per_warp = (int)(fill < 1 ? 1 : (fill > 32 / lanes ? 32 / lanes : fill));
     const int lines_per_warp = plan.lines_per_warp;
     for (int k = 0; k < 8; ++k) {
         const int dir = order[k];

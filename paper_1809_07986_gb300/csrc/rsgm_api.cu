@@ -29,6 +29,7 @@ struct rsgm_stream_s {
     int nbits;
     int nplanes;      // enabled path directions
     int lanes;        // lanes per path line in the aggregation kernel
+    int sm_count;     // multiprocessors of the handle's device
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
     bool has_state;
@@ -202,7 +203,7 @@ int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr)
     RSGM_MARK(s, 3);
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
-    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->st));
+    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, s->st));
     RSGM_MARK(s, 5);
     RSGM_CUDA(launch_update(s->buf, g, fp, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
@@ -267,6 +268,10 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
     s->P = *p;
     s->st = (cudaStream_t)cuda_stream;
     s->device = dev;
+    if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        s->sm_count = 0;
+    }
     s->g.B = p->batch;
     s->g.W = p->width;
     s->g.H = p->height;

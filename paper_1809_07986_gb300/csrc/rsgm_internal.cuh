@@ -38,7 +38,7 @@ struct PathPlan {
     Geometry g;
     int P1, P2;
     int lanes;           // lanes per line for narrow pixels (the common window width)
-    int lines_per_warp;  // 32 / lanes
+    int lines_per_warp;  // <= 32 / lanes
     int ndir;
     int dir[8];
     int plane_of[8];
@@ -93,7 +93,7 @@ cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStre
 // `lanes` lanes per path line, planes of `plane_bytes` (1 or 2) per cell.
 int lanes_per_line(int widest_narrow_window);
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         int lanes, int plane_bytes, cudaStream_t st);
+                         int lanes, int plane_bytes, int sm_count, cudaStream_t st);
 
 // Sum of the planes, winner-takes-all, Kalman correction and gate
 // (Sections 2.2-2.4).
