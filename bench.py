@@ -382,6 +382,22 @@ def run_ours(args, rank, world, local_rank):
         result["latency_ms"] = {"p50": q(0.5), "p99": q(0.99), "frames": len(lat), "streams": 1,
                                 "stage_ms": {k: v / max(n1, 1) for k, v in st1.items()}}
 
+        # ---- after the path: 3x3 median output and moving-object boxes
+        dp = rs.rsgm_default_detect_params()
+        med = torch.empty(B, H, W, device=dev)
+        with torch.cuda.stream(stream):
+            rs.rsgm_median(gs.handle, med)
+            rs.rsgm_detect(gs.handle, dp, B)
+            gs.sync()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                rs.rsgm_median(gs.handle, med)
+                boxes, counts = rs.rsgm_detect(gs.handle, dp, B)
+            t_post = (time.perf_counter() - t0) / 5
+        result["post_path"] = {"median_and_boxes_ms_per_step": 1e3 * t_post,
+                               "boxes_per_stream": float(np.mean(counts)),
+                               "note": "3x3 median + integral image + windows on the GPU, grouping on the host"}
+
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)
     gs.close()

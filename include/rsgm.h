@@ -166,6 +166,54 @@ int rsgm_read_buffer(rsgm_stream s, int which, void *dst, size_t capacity, size_
  * (summed over frames) since init; cells of the last frame.  Synchronises. */
 int rsgm_counters(rsgm_stream s, uint64_t *frames, uint64_t *cells, uint64_t *last_cells);
 
+/*
+ * Displayed disparity: the 3x3 median of the current state's d (Section 2.3:
+ * a block median filter in postprocessing, outside the Kalman loop, so it
+ * does not change the state).  Border pixels use clamped coordinates.  out:
+ * B*H*W floats, device or host (host: call rsgm_sync before reading).
+ */
+int rsgm_median(rsgm_stream s, float *out);
+
+/* Moving-object boxes (Section 4), half-open pixel rectangles. */
+typedef struct {
+    int32_t x0, y0, x1, y1;
+} rsgm_box;
+
+#define RSGM_MAX_WINDOW_SIZES 8
+
+/*
+ * Parameters of the box detection.  Defaults (rsgm_default_detect_params):
+ * window sizes 20x20, 30x30, 40x40, 50x50, 50x75 (the paper's range is 20x20
+ * to 50x75), stride 10 px, the upper third of the image skipped (1/3),
+ * detection when the window's mean |d_pred - d_meas| exceeds 1 px, grouping
+ * while any IoU > 0/1 (any overlap), boxes under 1500 px^2 dropped.  The
+ * paper gives no numbers beyond the window range and the skipped third;
+ * these are readings.
+ */
+typedef struct {
+    int32_t nsizes;                              /* 1 .. RSGM_MAX_WINDOW_SIZES */
+    int32_t sizes[RSGM_MAX_WINDOW_SIZES][2];     /* (width, height) >= 1 */
+    int32_t stride;                              /* window grid step, >= 1 */
+    int32_t skip_num, skip_den;                  /* rows y < H * skip_num / skip_den are not searched */
+    float thresh_px;                             /* mean |nu| threshold, >= 0 */
+    int32_t iou_num, iou_den;                    /* group while IoU > iou_num / iou_den */
+    int32_t min_area;                            /* smaller final boxes are dropped */
+} rsgm_detect_params;
+
+int rsgm_default_detect_params(rsgm_detect_params *p);
+
+/*
+ * Boxes of the latest frame, for every stream: the |d_pred - d_meas| map
+ * (quantised to 1/16 px; 0 where there was no prediction) is summed over
+ * sliding windows with an integral image (inclusion-exclusion); windows whose
+ * mean exceeds the threshold are grouped greedily (the pair of highest IoU is
+ * replaced by its bounding box until no pair exceeds the IoU threshold) and
+ * small boxes are dropped.  boxes: host array of B * capacity boxes (stream b
+ * at b * capacity); counts: host array of B (the number found, which may
+ * exceed capacity: only the first `capacity` are written).  Synchronises.
+ */
+int rsgm_detect(rsgm_stream s, const rsgm_detect_params *p, rsgm_box *boxes, int32_t capacity, int32_t *counts);
+
 /* Stage timing.  While enabled, every frame records CUDA events on the
  * handle's stream around its stages: RSGM_STAGE_PREDICT (splat, hole fill,
  * reset, window), _SCAN (cell offsets), _CENSUS, _COST, _AGGREGATE (all path

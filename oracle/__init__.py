@@ -77,6 +77,13 @@ def lib():
             L.orc_kalman_update32.argtypes = [f32, f32, i32, f32, f32, f32, P, P, P, P]
             L.orc_kalman32.argtypes = [P, P, P, P, i64, f32, f32, P, P, P, P]
             L.orc_kalman64.argtypes = [P, P, P, P, i64, f32, f32, P, P]
+            L.orc_median3.argtypes = [P, i32, i32, P]
+            L.orc_abs_innovation_q.argtypes = [P, P, i64, P]
+            L.orc_integral.argtypes = [P, i32, i32, P]
+            L.orc_windows.argtypes = [P, i32, i32, P, i32, i32, i32, ctypes.c_uint32, P, i32]
+            L.orc_windows.restype = i32
+            L.orc_merge_boxes.argtypes = [P, i32, i64, i64, i64]
+            L.orc_merge_boxes.restype = i32
             _lib = L
     return _lib
 
@@ -296,3 +303,71 @@ def frame(P: Params, left: np.ndarray, right: np.ndarray, state=None, motion=Non
                cost=cv, S=S, d_int=d_int, d_z=d_z, d=d, p=p, mask=mask, nu=nu,
                d64=d64, p64=p64)
     return out
+
+
+# ---------------------------------------------------------------- after the path (Sections 2.3, 4)
+
+def median3(d):
+    d = _f32(d)
+    H, W = d.shape
+    out = np.zeros((H, W), np.float32)
+    lib().orc_median3(_p(d), W, H, _p(out))
+    return out
+
+
+def abs_innovation_q(nu, cls):
+    nu = _f32(nu)
+    cls = np.ascontiguousarray(cls, np.uint8)
+    a = np.zeros(nu.shape, np.uint32)
+    lib().orc_abs_innovation_q(_p(nu), _p(cls), nu.size, _p(a))
+    return a
+
+
+def integral(a):
+    a = np.ascontiguousarray(a, np.uint32)
+    H, W = a.shape
+    sat = np.zeros((H + 1, W + 1), np.uint64)
+    lib().orc_integral(_p(a), W, H, _p(sat))
+    return sat
+
+
+def windows(sat, sizes, stride, y_min, thresh_q, cap=1 << 16):
+    sat = np.ascontiguousarray(sat, np.uint64)
+    H, W = sat.shape[0] - 1, sat.shape[1] - 1
+    sz = np.ascontiguousarray(np.asarray(sizes, np.int32).reshape(-1))
+    boxes = np.zeros((cap, 4), np.int32)
+    n = lib().orc_windows(_p(sat), W, H, _p(sz), len(sz) // 2, stride, y_min, int(thresh_q), _p(boxes), cap)
+    return boxes[:n].copy()
+
+
+def merge_boxes(boxes, iou_num, iou_den, min_area):
+    b = np.ascontiguousarray(np.asarray(boxes, np.int32).reshape(-1, 4)).copy()
+    n = lib().orc_merge_boxes(_p(b), len(b), iou_num, iou_den, min_area)
+    return b[:n].copy()
+
+
+@dataclasses.dataclass
+class DetectParams:
+    """Moving-object boxes (Section 4).  Window sizes span the paper's 20x20
+    to 50x75; the rest are readings."""
+    sizes: tuple = ((20, 20), (30, 30), (40, 40), (50, 50), (50, 75))
+    stride: int = 10
+    skip_top_fraction_num: int = 1        # upper third skipped: y_min = H * 1 / 3
+    skip_top_fraction_den: int = 3
+    thresh_px: float = 1.0                # mean |d_pred - d_meas| of a detection window, px
+    iou_num: int = 0                      # merge while some IoU > iou_num / iou_den
+    iou_den: int = 1
+    min_area: int = 1500                  # smaller boxes are discarded
+
+    def y_min(self, H):
+        return H * self.skip_top_fraction_num // self.skip_top_fraction_den
+
+    def thresh_q(self):
+        return int(np.floor(np.float32(self.thresh_px) * np.float32(16.0) + np.float32(0.5)))
+
+
+def detect(nu, cls, D: DetectParams):
+    H, W = nu.shape
+    sat = integral(abs_innovation_q(nu, cls))
+    raw = windows(sat, D.sizes, D.stride, D.y_min(H), D.thresh_q())
+    return merge_boxes(raw, D.iou_num, D.iou_den, D.min_area), raw, sat

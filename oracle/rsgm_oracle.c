@@ -510,3 +510,160 @@ void orc_kalman64(const float *d_pred, const float *p_pred, const uint8_t *cls, 
         p[i] = (1.0 - K) * (1.0 - K) * pv + K * K * rr;
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* After the path: the displayed map and moving-object boxes.            */
+/* ------------------------------------------------------------------ */
+
+/*
+ * 3x3 median of the disparity map (Section 2.3: a block median filter of 3x3
+ * pixels in postprocessing, outside the Kalman loop).  Reading: border pixels
+ * use clamped coordinates; the median of 9 values is the 5th smallest.
+ */
+void orc_median3(const float *d, int W, int H, float *out)
+{
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            float v[9];
+            int n = 0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++)
+                    v[n++] = d[clampi(y + dy, 0, H - 1) * W + clampi(x + dx, 0, W - 1)];
+            for (int i = 1; i < 9; i++) { /* insertion sort */
+                float t = v[i];
+                int j = i - 1;
+                while (j >= 0 && v[j] > t) {
+                    v[j + 1] = v[j];
+                    j--;
+                }
+                v[j + 1] = t;
+            }
+            out[y * W + x] = v[4];
+        }
+    }
+}
+
+/*
+ * |d_pred - d_meas| per pixel (Section 4), quantised to 1/16 px so that the
+ * sums below are exact integers: a = floor(|nu| * 16 + 0.5), capped at 65535;
+ * pixels without a prediction (cls 2) contribute 0.  Single precision.
+ */
+void orc_abs_innovation_q(const float *nu, const uint8_t *cls, int64_t n, uint32_t *a)
+{
+    for (int64_t i = 0; i < n; i++) {
+        if (cls[i] == 2) {
+            a[i] = 0;
+            continue;
+        }
+        float q = floorf(fabsf(nu[i]) * 16.0f + 0.5f);
+        a[i] = q > 65535.0f ? 65535u : (uint32_t)q;
+    }
+}
+
+/* Summed-area table with a zero first row and column: sat[(y+1)(W+1) + x+1] =
+ * sum of a over [0, x] x [0, y] (Section 4: sub-matrix sums in constant time
+ * by inclusion-exclusion). */
+void orc_integral(const uint32_t *a, int W, int H, uint64_t *sat)
+{
+    for (int x = 0; x <= W; x++) sat[x] = 0;
+    for (int y = 0; y < H; y++) {
+        uint64_t row = 0;
+        sat[(y + 1) * (W + 1)] = 0;
+        for (int x = 0; x < W; x++) {
+            row += a[y * W + x];
+            sat[(y + 1) * (W + 1) + x + 1] = sat[y * (W + 1) + x + 1] + row;
+        }
+    }
+}
+
+/*
+ * Sliding windows (Section 4): for every window size (ww, wh), top-left
+ * corners on a `stride` grid with y0 >= y_min (the paper skips the upper third
+ * of the image), windows inside the image; a window is a detection when its
+ * sum exceeds thresh_q * area (mean |nu| above the threshold, in the same
+ * 1/16 px units).  Writes the detections' boxes [x0, x1) x [y0, y1) in
+ * size, then row, then column order; returns how many (at most cap).
+ */
+int orc_windows(const uint64_t *sat, int W, int H, const int *sizes, int nsizes, int stride, int y_min,
+                uint32_t thresh_q, int32_t *boxes, int cap)
+{
+    int n = 0;
+    for (int s = 0; s < nsizes; s++) {
+        int ww = sizes[2 * s], wh = sizes[2 * s + 1];
+        for (int y0 = y_min; y0 + wh <= H; y0 += stride) {
+            for (int x0 = 0; x0 + ww <= W; x0 += stride) {
+                int x1 = x0 + ww, y1 = y0 + wh;
+                uint64_t sum = sat[y1 * (W + 1) + x1] - sat[y0 * (W + 1) + x1] - sat[y1 * (W + 1) + x0] +
+                               sat[y0 * (W + 1) + x0];
+                if (sum > (uint64_t)thresh_q * (uint64_t)(ww * wh)) {
+                    if (n < cap) {
+                        boxes[4 * n] = x0;
+                        boxes[4 * n + 1] = y0;
+                        boxes[4 * n + 2] = x1;
+                        boxes[4 * n + 3] = y1;
+                    }
+                    n++;
+                }
+            }
+        }
+    }
+    return n < cap ? n : cap;
+}
+
+static int64_t box_area(const int32_t *b) { return (int64_t)(b[2] - b[0]) * (b[3] - b[1]); }
+
+static int64_t box_inter(const int32_t *a, const int32_t *b)
+{
+    int32_t x0 = a[0] > b[0] ? a[0] : b[0], y0 = a[1] > b[1] ? a[1] : b[1];
+    int32_t x1 = a[2] < b[2] ? a[2] : b[2], y1 = a[3] < b[3] ? a[3] : b[3];
+    if (x1 <= x0 || y1 <= y0) return 0;
+    return (int64_t)(x1 - x0) * (y1 - y0);
+}
+
+/*
+ * Greedy grouping (Section 4): as long as some pair of boxes overlaps with
+ * intersection-over-union above iou_num / iou_den, the pair with the highest
+ * IoU is replaced by the smallest box containing both; then boxes smaller
+ * than min_area are discarded.  Readings: IoU compared exactly as fractions
+ * of integer areas; ties go to the lexicographically smallest pair (i, j),
+ * i < j; the union takes the place of box i and box j is removed, keeping
+ * the order of the others.  Works in place; returns the number of boxes.
+ */
+int orc_merge_boxes(int32_t *boxes, int n, int64_t iou_num, int64_t iou_den, int64_t min_area)
+{
+    for (;;) {
+        int bi = -1, bj = -1;
+        int64_t bn = 0, bd = 1; /* best IoU as a fraction */
+        for (int i = 0; i < n; i++) {
+            for (int j = i + 1; j < n; j++) {
+                int64_t in = box_inter(boxes + 4 * i, boxes + 4 * j);
+                if (in == 0) continue;
+                int64_t un = box_area(boxes + 4 * i) + box_area(boxes + 4 * j) - in;
+                /* above the threshold: in / un > iou_num / iou_den */
+                if (!(in * iou_den > iou_num * un)) continue;
+                if (bi < 0 || in * bd > bn * un) {
+                    bi = i;
+                    bj = j;
+                    bn = in;
+                    bd = un;
+                }
+            }
+        }
+        if (bi < 0) break;
+        int32_t *a = boxes + 4 * bi, *b = boxes + 4 * bj;
+        if (b[0] < a[0]) a[0] = b[0];
+        if (b[1] < a[1]) a[1] = b[1];
+        if (b[2] > a[2]) a[2] = b[2];
+        if (b[3] > a[3]) a[3] = b[3];
+        for (int k = bj; k + 1 < n; k++)
+            for (int c = 0; c < 4; c++) boxes[4 * k + c] = boxes[4 * (k + 1) + c];
+        n--;
+    }
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        if (box_area(boxes + 4 * i) < min_area) continue;
+        for (int c = 0; c < 4; c++) boxes[4 * m + c] = boxes[4 * i + c];
+        m++;
+    }
+    return m;
+}

@@ -59,6 +59,20 @@ class rsgm_params(ctypes.Structure):
     ]
 
 
+RSGM_MAX_WINDOW_SIZES = 8
+
+
+class rsgm_box(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_int32), ("y0", ctypes.c_int32), ("x1", ctypes.c_int32), ("y1", ctypes.c_int32)]
+
+
+class rsgm_detect_params(ctypes.Structure):
+    _fields_ = [("nsizes", ctypes.c_int32), ("sizes", (ctypes.c_int32 * 2) * RSGM_MAX_WINDOW_SIZES),
+                ("stride", ctypes.c_int32), ("skip_num", ctypes.c_int32), ("skip_den", ctypes.c_int32),
+                ("thresh_px", ctypes.c_float), ("iou_num", ctypes.c_int32), ("iou_den", ctypes.c_int32),
+                ("min_area", ctypes.c_int32)]
+
+
 class RsgmError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str):
         super().__init__("%s failed: %s (%d): %s" % (where, status_string(code), code, detail))
@@ -79,6 +93,9 @@ SIGNATURES = {
     "rsgm_read_buffer": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "rsgm_counters": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "rsgm_median": (ctypes.c_int, [_P, _P]),
+    "rsgm_default_detect_params": (ctypes.c_int, [ctypes.POINTER(rsgm_detect_params)]),
+    "rsgm_detect": (ctypes.c_int, [_P, ctypes.POINTER(rsgm_detect_params), _P, ctypes.c_int32, _P]),
     "rsgm_enable_stage_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "rsgm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_window_offsets_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
@@ -211,6 +228,32 @@ def rsgm_counters(h: int):
     f, c, l = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib().rsgm_counters(h, ctypes.byref(f), ctypes.byref(c), ctypes.byref(l)), "rsgm_counters")
     return f.value, c.value, l.value
+
+
+def rsgm_median(h: int, out):
+    _check(lib().rsgm_median(h, _ptr(out)), "rsgm_median")
+
+
+def rsgm_default_detect_params(**overrides) -> rsgm_detect_params:
+    p = rsgm_detect_params()
+    _check(lib().rsgm_default_detect_params(ctypes.byref(p)), "rsgm_default_detect_params")
+    for k, v in overrides.items():
+        if k == "sizes":
+            p.nsizes = len(v)
+            for i, (w, hh) in enumerate(v):
+                p.sizes[i][0], p.sizes[i][1] = w, hh
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def rsgm_detect(h: int, params: rsgm_detect_params, batch: int, capacity: int = 256):
+    """Returns a list (one per stream) of numpy arrays of boxes (x0, y0, x1, y1)."""
+    import numpy as np
+    boxes = np.zeros((batch, max(capacity, 1), 4), np.int32)
+    counts = np.zeros(batch, np.int32)
+    _check(lib().rsgm_detect(h, ctypes.byref(params), _ptr(boxes), capacity, _ptr(counts)), "rsgm_detect")
+    return [boxes[b, :min(int(counts[b]), capacity)].copy() for b in range(batch)], counts
 
 
 def rsgm_enable_stage_timing(h: int, enable: bool = True):

@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <math.h>
+
 #include <new>
 
 #include "rsgm_internal.cuh"
@@ -135,7 +137,8 @@ void free_buffers(Buffers &b)
 {
     void *ptrs[] = {b.img_l, b.img_r, b.cen_l, b.cen_r, b.d,    b.p,    b.key,       b.d_pred,
                     b.p_pred, b.win, b.cls,   b.inrow, b.meta, b.row_total, b.row_base, b.cost,
-                    b.planes, b.S,   b.d_int, b.mask,  b.d_z,  b.nu,   b.counters};
+                    b.planes, b.S,   b.d_int, b.mask,  b.d_z,  b.nu,   b.counters, b.median,
+                    b.sat,    b.flags};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(&b, 0, sizeof(b));
@@ -290,7 +293,7 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
     Buffers &b = s->buf;
     const size_t n = (size_t)s->g.NPIX, rows = (size_t)p->batch * p->height;
     const size_t cells = n * (size_t)p->max_disp;
-    void *all[32];
+    void *all[40];
     int nall = 0;
     if ((rc = alloc(&b.img_l, n, all, nall)) || (rc = alloc(&b.img_r, n, all, nall)) ||
         (rc = alloc(&b.cen_l, n, all, nall)) || (rc = alloc(&b.cen_r, n, all, nall)) ||
@@ -303,7 +306,10 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc((uint8_t **)&b.planes, (size_t)plane_stride(s->g) * s->nplanes * s->plane_bytes, all, nall)) ||
         (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
         (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
-        (rc = alloc(&b.nu, n, all, nall)) || (rc = alloc(&b.counters, 4, all, nall))) {
+        (rc = alloc(&b.nu, n, all, nall)) || (rc = alloc(&b.counters, 4, all, nall)) ||
+        (rc = alloc(&b.median, n, all, nall)) ||
+        (rc = alloc(&b.sat, (size_t)p->batch * (p->height + 1) * (p->width + 1), all, nall)) ||
+        (rc = alloc(&b.flags, n * RSGM_MAX_WINDOW_SIZES, all, nall))) {
         free_buffers(b);
         delete s;
         return rc;
@@ -466,6 +472,82 @@ int rsgm_counters(rsgm_stream s, uint64_t *frames, uint64_t *cells, uint64_t *la
     if (frames) *frames = h[0];
     if (cells) *cells = h[1];
     if (last_cells) *last_cells = h[2];
+    return RSGM_OK;
+}
+
+int rsgm_median(rsgm_stream s, float *out)
+{
+    if (!s || !out) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or output");
+    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "no frame processed yet");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    RSGM_CUDA(launch_median3(s->buf.d, s->buf.median, s->g, s->st));
+    RSGM_CUDA(cudaMemcpyAsync(out, s->buf.median, (size_t)s->g.NPIX * sizeof(float), cudaMemcpyDefault, s->st));
+    return RSGM_OK;
+}
+
+int rsgm_default_detect_params(rsgm_detect_params *p)
+{
+    if (!p) return fail(RSGM_ERR_INVALID_ARG, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    const int sizes[5][2] = {{20, 20}, {30, 30}, {40, 40}, {50, 50}, {50, 75}};
+    p->nsizes = 5;
+    for (int i = 0; i < 5; ++i) {
+        p->sizes[i][0] = sizes[i][0];
+        p->sizes[i][1] = sizes[i][1];
+    }
+    p->stride = 10;
+    p->skip_num = 1;
+    p->skip_den = 3;
+    p->thresh_px = 1.0f;
+    p->iou_num = 0;
+    p->iou_den = 1;
+    p->min_area = 1500;
+    return RSGM_OK;
+}
+
+int rsgm_detect(rsgm_stream s, const rsgm_detect_params *p, rsgm_box *boxes, int32_t capacity, int32_t *counts)
+{
+    if (!s || !p || !counts || capacity < 0 || (capacity > 0 && !boxes))
+        return fail(RSGM_ERR_INVALID_ARG, "NULL handle, params, boxes or counts");
+    if (p->nsizes < 1 || p->nsizes > RSGM_MAX_WINDOW_SIZES || p->stride < 1 || p->skip_den < 1 ||
+        p->skip_num < 0 || p->skip_num > p->skip_den || p->iou_den < 1 || p->iou_num < 0 || p->min_area < 0 ||
+        !(p->thresh_px >= 0.0f) || p->thresh_px > 4096.0f)
+        return fail(RSGM_ERR_INVALID_ARG, "detection parameters out of range");
+    for (int i = 0; i < p->nsizes; ++i)
+        if (p->sizes[i][0] < 1 || p->sizes[i][1] < 1) return fail(RSGM_ERR_INVALID_ARG, "window size < 1");
+    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "no frame processed yet");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    const Geometry &g = s->g;
+    DetectPlan dp;
+    memset(&dp, 0, sizeof(dp));
+    dp.nsizes = p->nsizes;
+    dp.stride = p->stride;
+    dp.y_min = (int)((long long)g.H * p->skip_num / p->skip_den);
+    dp.thresh_q = (unsigned)floorf(p->thresh_px * 16.0f + 0.5f);
+    for (int i = 0; i < p->nsizes; ++i) {
+        dp.size[i][0] = p->sizes[i][0];
+        dp.size[i][1] = p->sizes[i][1];
+        dp.nx[i] = p->sizes[i][0] <= g.W ? (g.W - p->sizes[i][0]) / p->stride + 1 : 0;
+        dp.ny[i] = dp.y_min + p->sizes[i][1] <= g.H ? (g.H - p->sizes[i][1] - dp.y_min) / p->stride + 1 : 0;
+        dp.first[i + 1] = dp.first[i] + dp.nx[i] * dp.ny[i];
+    }
+    dp.total = dp.first[p->nsizes];
+    RSGM_CUDA(launch_detect_windows(s->buf, g, dp, s->st));
+    const size_t nflags = (size_t)g.B * dp.total;
+    uint8_t *flags = (uint8_t *)malloc(nflags ? nflags : 1);
+    if (!flags) return fail(RSGM_ERR_OOM, "host allocation failed");
+    cudaError_t e = nflags ? cudaMemcpyAsync(flags, s->buf.flags, nflags, cudaMemcpyDeviceToHost, s->st) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+        free(flags);
+        return cuda_fail(e, "detection flags");
+    }
+    for (int b = 0; b < g.B; ++b)
+        counts[b] = group_boxes(flags + (size_t)b * dp.total, dp, p->iou_num, p->iou_den, p->min_area,
+                                capacity > 0 ? (int32_t *)(boxes + (size_t)b * capacity) : nullptr, capacity);
+    free(flags);
     return RSGM_OK;
 }
 

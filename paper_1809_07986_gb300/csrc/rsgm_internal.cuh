@@ -46,6 +46,18 @@ struct PathPlan {
     long long plane_stride;  // elements between consecutive planes
 };
 
+// Sliding-window plan of the moving-object boxes (Section 4): windows of size
+// s are numbered first[s] + row * nx[s] + column.
+struct DetectPlan {
+    int nsizes;
+    int size[RSGM_MAX_WINDOW_SIZES][2];
+    int nx[RSGM_MAX_WINDOW_SIZES], ny[RSGM_MAX_WINDOW_SIZES];
+    int first[RSGM_MAX_WINDOW_SIZES + 1];
+    int total;
+    int stride, y_min;
+    unsigned thresh_q;  // mean |nu| threshold in 1/16 px
+};
+
 // Per-frame scalar parameters of the resolve / update kernels.
 struct FrameParams {
     int radius_mode, radius;
@@ -72,6 +84,9 @@ struct Buffers {
     uint8_t *mask;
     float *d_z, *nu;
     unsigned long long *counters;       // [0] frames, [1] cells, [2] cells of the last frame
+    float *median;                      // 3x3 median of d, NPIX
+    unsigned long long *sat;            // integral image of |nu|, B * (H+1) * (W+1)
+    uint8_t *flags;                     // detection flag per window, B * RSGM_MAX_WINDOW_SIZES * H * W
 };
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
@@ -99,5 +114,11 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
 // (Sections 2.2-2.4).
 cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, int nplanes,
                           int plane_bytes, cudaStream_t st);
+
+// After the path (Section 2.3 median output, Section 4 boxes).
+cudaError_t launch_median3(const float *d, float *out, const Geometry &g, cudaStream_t st);
+cudaError_t launch_detect_windows(const Buffers &b, const Geometry &g, const DetectPlan &dp, cudaStream_t st);
+int group_boxes(const uint8_t *flags, const DetectPlan &dp, int iou_num, int iou_den, long long min_area,
+                int32_t *out, int capacity);
 
 }  // namespace rsgm
