@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=32, help="camera streams per GPU")
     ap.add_argument("--radius", type=int, default=4)
+    ap.add_argument("--mixed", action="store_true",
+                    help="also time the mixed-resolution group (6x640x480/D64, 6x1242x375/D128, 4x1920x1080/D256)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-form, latency, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -215,6 +217,61 @@ def cpu_baseline(args, left, right, Rm, tv, K, budget_s=12.0):
     fps = len(times) / sum(times)
     return {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": "stream 0, reduced frames 1..%d (r=%d, 8 paths), single thread" % (len(times), args.radius)}
+
+
+# ------------------------------------------------------------------ mixed-resolution group
+
+MIXED = [(6, 640, 480, 64, 400.0), (6, 1242, 375, 128, 721.0), (4, 1920, 1080, 256, 1000.0)]
+
+
+def mixed_group(args, dev, stream):
+    """16 streams of three resolutions advanced by one CUDA graph launch per
+    tick, each member with its autotuned aggregation schedule."""
+    import torch
+    import synth
+    import paper_1809_07986_gb300 as rs
+    nframes = 1 + args.warmup + args.steps
+    members, data = [], []
+    for gi, (B, Wm, Hm, Dm, f) in enumerate(MIXED):
+        seqs = [synth.kitti_like_sequence(5000 + 100 * gi + b, n_frames=max(100, nframes), width=Wm, height=Hm,
+                                          f=f, baseline=BASE, device=dev, render_frames=nframes)
+                for b in range(B)]
+        data.append(dict(L=torch.stack([q["left"] for q in seqs], 1).contiguous(),
+                         R=torch.stack([q["right"] for q in seqs], 1).contiguous(),
+                         Rm=torch.stack([q["R"] for q in seqs], 1).contiguous(),
+                         t=torch.stack([q["t"] for q in seqs], 1).contiguous(), K=seqs[0]["K"]))
+        members.append(rs.Stream(rs.rsgm_default_params(Wm, Hm, max_disp=Dm, radius=args.radius, batch=B), stream))
+    group = rs.rsgm_group_create([m.handle for m in members])
+    tuned = []
+
+    def tick(k):
+        rs.rsgm_group_reduced_frame(group, [x["L"][k] for x in data], [x["R"][k] for x in data],
+                                    [x["Rm"][k] for x in data], [x["t"][k] for x in data],
+                                    [x["K"] for x in data], [BASE] * len(data))
+
+    with torch.cuda.stream(stream):
+        for m, x in zip(members, data):
+            m.full_frame(x["L"][0], x["R"][0])
+        tick(1)
+        for m in members:
+            tuned.append(rs.rsgm_autotune(m.handle))
+        for k in range(2, 1 + args.warmup):
+            tick(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(1 + args.warmup, nframes):
+            tick(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    rs.rsgm_group_destroy(group)
+    for m in members:
+        m.close()
+    nstreams = sum(g[0] for g in MIXED)
+    return {"frames_per_s": nstreams * args.steps / el, "ms_per_tick": 1e3 * el / args.steps,
+            "streams": "6x640x480/D64 + 6x1242x375/D128 + 4x1920x1080/D256",
+            "graph_launches_per_tick": 1, "lines_per_warp_tuned": tuned}
 
 
 # ------------------------------------------------------------------ our arm
@@ -397,6 +454,9 @@ def run_ours(args, rank, world, local_rank):
         result["post_path"] = {"median_and_boxes_ms_per_step": 1e3 * t_post,
                                "boxes_per_stream": float(np.mean(counts)),
                                "note": "3x3 median + integral image + windows on the GPU, grouping on the host"}
+
+        if args.mixed and rank == 0:
+            result["mixed_group"] = mixed_group(args, dev, stream)
 
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)

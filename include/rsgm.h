@@ -261,6 +261,36 @@ int rsgm_stage_times(rsgm_stream s, double *ms, int32_t *frames);
 int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t rows,
                                 uint32_t *offsets, uint32_t *total, void *cuda_stream);
 
+/*
+ * Schedule autotuner.  Times the aggregation kernel (Eq. 1) on the handle's
+ * latest frame with each candidate number of path lines per warp and keeps
+ * the fastest for later frames (written to *lines_per_warp if not NULL).
+ * Results do not depend on the choice; only speed does.  Requires a
+ * processed frame; synchronises.
+ */
+int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp);
+
+/*
+ * A group advances several handles of possibly different geometry by one
+ * reduced frame each in a single CUDA graph launch: every member's launches
+ * are captured on a stream of its own (forked from and joined back into one),
+ * so members run concurrently, and the executable graph is updated in place
+ * from tick to tick.  Members must share one device and one CUDA stream (the
+ * graph is launched on it) and stay alive while the group exists; the group
+ * does not own them.
+ */
+typedef struct rsgm_group_s *rsgm_group;
+int rsgm_group_create(rsgm_group *out, rsgm_stream *members, int32_t n);
+
+/* One reduced frame of every member k: left[k], right[k] are device images
+ * (as in rsgm_reduced_frame), R[k], t[k], K[k] host arrays, baseline[k]. */
+int rsgm_group_reduced_frame(rsgm_group g, const uint8_t *const *left, const uint8_t *const *right,
+                             const float *const *R, const float *const *t, const float *const *K,
+                             const float *baseline);
+
+/* Waits for the group's work and frees it (not its members).  NULL is a no-op. */
+int rsgm_group_destroy(rsgm_group g);
+
 /* Waits for the handle's enqueued work; reports deferred device errors. */
 int rsgm_sync(rsgm_stream s);
 

@@ -99,6 +99,11 @@ SIGNATURES = {
     "rsgm_enable_stage_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "rsgm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_window_offsets_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "rsgm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "rsgm_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32]),
+    "rsgm_group_reduced_frame": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                                ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
+    "rsgm_group_destroy": (ctypes.c_int, [_P]),
     "rsgm_sync": (ctypes.c_int, [_P]),
     "rsgm_destroy_stream": (ctypes.c_int, [_P]),
     "rsgm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -275,6 +280,35 @@ def rsgm_window_offsets_noalloc(windows, width: int, rows: int, offsets, total=N
         cuda_stream = cuda_stream.cuda_stream
     _check(lib().rsgm_window_offsets_noalloc(_ptr(windows), width, rows, _ptr(offsets), _ptr(total),
                                              cuda_stream), "rsgm_window_offsets_noalloc")
+
+
+def rsgm_autotune(h: int) -> int:
+    n = ctypes.c_int32()
+    _check(lib().rsgm_autotune(h, ctypes.byref(n)), "rsgm_autotune")
+    return n.value
+
+
+def rsgm_group_create(handles) -> int:
+    arr = (_P * len(handles))(*handles)
+    g = _P()
+    _check(lib().rsgm_group_create(ctypes.byref(g), arr, len(handles)), "rsgm_group_create")
+    return g.value
+
+
+def rsgm_group_reduced_frame(g: int, lefts, rights, Rs, ts, Ks, baselines):
+    """Per member k: device images lefts[k], rights[k]; host R (B x 3 x 3),
+    t (B x 3), K (3 x 3); baseline.  Host arrays are kept alive for the call."""
+    import numpy as np
+    n = len(lefts)
+    keep = [_host_f32(x) for x in Rs] + [_host_f32(x) for x in ts] + [_host_f32(x, 9) for x in Ks]
+    P = lambda xs: (_P * n)(*[_ptr(x) for x in xs])
+    bl = np.ascontiguousarray(np.asarray(baselines, np.float32))
+    _check(lib().rsgm_group_reduced_frame(g, P(lefts), P(rights), P(keep[:n]), P(keep[n:2 * n]),
+                                          P(keep[2 * n:]), _ptr(bl)), "rsgm_group_reduced_frame")
+
+
+def rsgm_group_destroy(g: int):
+    _check(lib().rsgm_group_destroy(g), "rsgm_group_destroy")
 
 
 def rsgm_sync(h: int):

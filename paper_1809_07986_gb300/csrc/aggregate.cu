@@ -247,7 +247,7 @@ int lanes_per_line(int window)
 }
 
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         int lanes, int plane_bytes, int sm_count, cudaStream_t st)
+                         int lanes, int plane_bytes, int sm_count, int lines_override, cudaStream_t st)
 {
     PathPlan plan;
     plan.g = g;
@@ -271,6 +271,7 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
         if (path_mask & (1u << dir)) total_lines += (long long)g.B * lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H);
     const long long fill = total_lines / ((long long)(sm_count > 0 ? sm_count : 152) * 32);
     plan.lines_per_warp = (int)(fill < 1 ? 1 : (fill > 32 / lanes ? 32 / lanes : fill));
+    if (lines_override > 0) plan.lines_per_warp = lines_override < 32 / lanes ? lines_override : 32 / lanes;
     const int lines_per_warp = plan.lines_per_warp;
     for (int k = 0; k < 8; ++k) {
         const int dir = order[k];

@@ -32,6 +32,8 @@ struct rsgm_stream_s {
     int nplanes;      // enabled path directions
     int lanes;        // lanes per path line in the aggregation kernel
     int sm_count;     // multiprocessors of the handle's device
+    int tuned_lines;  // aggregation lines per warp picked by rsgm_autotune (0: heuristic)
+    bool capturing;   // enqueueing into a group's graph: no stage-timing events
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
     bool has_state;
@@ -167,6 +169,7 @@ int stage_images(rsgm_stream s, const uint8_t *left, const uint8_t *right, const
     size_t bytes = (size_t)s->g.NPIX;
     *dl = left;
     *dr = right;
+    if (s->capturing) return RSGM_OK;  // group frames take device images (checked before the capture)
     if (!is_device_pointer(left)) {
         RSGM_CUDA(cudaMemcpyAsync(s->buf.img_l, left, bytes, cudaMemcpyHostToDevice, s->st));
         *dl = s->buf.img_l;
@@ -182,7 +185,7 @@ int stage_images(rsgm_stream s, const uint8_t *left, const uint8_t *right, const
 int mark(rsgm_stream s, int k)
 {
     StageTimer &t = s->timer;
-    if (!t.on || t.n >= kMaxTimedFrames) return RSGM_OK;
+    if (!t.on || t.n >= kMaxTimedFrames || s->capturing) return RSGM_OK;
     RSGM_CUDA(cudaEventRecord(t.ev[t.n * (RSGM_NUM_STAGES + 1) + k], s->st));
     if (k == RSGM_NUM_STAGES) t.n++;
     return RSGM_OK;
@@ -206,11 +209,59 @@ int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr)
     RSGM_MARK(s, 3);
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
-    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, s->st));
+    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, s->tuned_lines, s->st));
     RSGM_MARK(s, 5);
     RSGM_CUDA(launch_update(s->buf, g, fp, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
     return RSGM_OK;
+}
+
+int check_reduced_args(rsgm_stream s, const uint8_t *left, const uint8_t *right, const float *R, const float *t,
+                       const float *K, float baseline)
+{
+    if (!s || !left || !right || !R || !t || !K)
+        return fail(RSGM_ERR_INVALID_ARG, "NULL handle, image or motion array");
+    if (!(baseline > 0.0f) || !(K[0] > 0.0f) || !(K[4] > 0.0f) || K[1] != 0.0f || K[3] != 0.0f ||
+        K[6] != 0.0f || K[7] != 0.0f || K[8] != 1.0f)
+        return fail(RSGM_ERR_INVALID_ARG, "K must be [fx 0 cx; 0 fy cy; 0 0 1] with fx, fy > 0; baseline > 0");
+    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "reduced frame before any full frame or set_state");
+    return RSGM_OK;
+}
+
+// Enqueues one reduced frame of all the handle's streams on s->st (arguments
+// already checked, the handle's device current).
+int enqueue_reduced(rsgm_stream s, const uint8_t *left, const uint8_t *right, const float *R, const float *t,
+                    const float *K, float baseline)
+{
+    const uint8_t *dl, *dr;
+    int rc = stage_images(s, left, right, &dl, &dr);
+    if (rc) return rc;
+    // The argument block is large but copied at launch: no host buffer outlives the call.
+    SplatArgs *a = (SplatArgs *)malloc(sizeof(SplatArgs));
+    if (!a) return fail(RSGM_ERR_OOM, "host allocation failed");
+    a->g = s->g;
+    a->fx = K[0];
+    a->cx = K[2];
+    a->fy = K[4];
+    a->cy = K[5];
+    a->fb = K[0] * baseline;
+    a->q = s->P.q;
+    for (int b = 0; b < s->g.B; ++b) {
+        memcpy(a->m[b].R, R + 9 * b, 9 * sizeof(float));
+        memcpy(a->m[b].t, t + 3 * b, 3 * sizeof(float));
+    }
+    rc = mark(s, 0);
+    if (rc) {
+        free(a);
+        return rc;
+    }
+    cudaError_t e = launch_splat(s->buf, *a, s->st);
+    free(a);
+    if (e != cudaSuccess) return cuda_fail(e, "splat launch");
+    RSGM_CUDA(launch_gather_fill(s->buf, s->g, s->P.q, s->st));
+    FrameParams fp = frame_params(s);
+    RSGM_CUDA(launch_window(s->buf, s->g, fp, s->st));
+    return match_and_update(s, dl, dr);
 }
 
 void destroy_timer(StageTimer &t)
@@ -346,43 +397,11 @@ int rsgm_full_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right)
 int rsgm_reduced_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right, const float *R,
                        const float *t, const float *K, float baseline)
 {
-    if (!s || !left || !right || !R || !t || !K)
-        return fail(RSGM_ERR_INVALID_ARG, "NULL handle, image or motion array");
-    if (!(baseline > 0.0f) || !(K[0] > 0.0f) || !(K[4] > 0.0f) || K[1] != 0.0f || K[3] != 0.0f ||
-        K[6] != 0.0f || K[7] != 0.0f || K[8] != 1.0f)
-        return fail(RSGM_ERR_INVALID_ARG, "K must be [fx 0 cx; 0 fy cy; 0 0 1] with fx, fy > 0; baseline > 0");
-    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "reduced frame before any full frame or set_state");
+    int rc = check_reduced_args(s, left, right, R, t, K, baseline);
+    if (rc) return rc;
     DeviceGuard dg(s->device);
     if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
-    const uint8_t *dl, *dr;
-    int rc = stage_images(s, left, right, &dl, &dr);
-    if (rc) return rc;
-    // The argument block is large but copied at launch: no host buffer outlives the call.
-    SplatArgs *a = (SplatArgs *)malloc(sizeof(SplatArgs));
-    if (!a) return fail(RSGM_ERR_OOM, "host allocation failed");
-    a->g = s->g;
-    a->fx = K[0];
-    a->cx = K[2];
-    a->fy = K[4];
-    a->cy = K[5];
-    a->fb = K[0] * baseline;
-    a->q = s->P.q;
-    for (int b = 0; b < s->g.B; ++b) {
-        memcpy(a->m[b].R, R + 9 * b, 9 * sizeof(float));
-        memcpy(a->m[b].t, t + 3 * b, 3 * sizeof(float));
-    }
-    rc = mark(s, 0);
-    if (rc) {
-        free(a);
-        return rc;
-    }
-    cudaError_t e = launch_splat(s->buf, *a, s->st);
-    free(a);
-    if (e != cudaSuccess) return cuda_fail(e, "splat launch");
-    RSGM_CUDA(launch_gather_fill(s->buf, s->g, s->P.q, s->st));
-    FrameParams fp = frame_params(s);
-    RSGM_CUDA(launch_window(s->buf, s->g, fp, s->st));
-    return match_and_update(s, dl, dr);
+    return enqueue_reduced(s, left, right, R, t, K, baseline);
 }
 
 int rsgm_state(rsgm_stream s, float *disp, float *var, uint8_t *moving_mask, int16_t *disp_int)
@@ -634,5 +653,194 @@ const char *rsgm_status_string(int code)
 }
 
 const char *rsgm_last_error(void) { return g_last_error; }
+
+// ------------------------------------------------------------------ groups
+
+int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "autotuning needs a processed frame");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    cudaEvent_t e0, e1;
+    RSGM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(RSGM_ERR_CUDA, "cudaEventCreate");
+    }
+    const int most = 32 / s->lanes;
+    int best = 0;
+    float best_ms = 0.0f;
+    int rc = RSGM_OK;
+    // Every candidate computes the same planes (each schedule is exact), so
+    // re-running the aggregation on the last frame's costs changes nothing.
+    for (int cand = 1; cand <= most && rc == RSGM_OK; cand = cand < most && cand * 2 > most ? most : cand * 2) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && rc == RSGM_OK; ++rep) {
+            cudaError_t e = cudaEventRecord(e0, s->st);
+            if (e == cudaSuccess)
+                e = launch_paths(s->buf, s->g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes,
+                                 s->sm_count, cand, s->st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+            if (t < ms) ms = t;
+        }
+        if (rc == RSGM_OK && (best == 0 || ms < best_ms)) {
+            best = cand;
+            best_ms = ms;
+        }
+        if (cand == most) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    s->tuned_lines = best;
+    if (lines_per_warp) *lines_per_warp = best;
+    return RSGM_OK;
+}
+
+}  // extern "C"
+
+struct rsgm_group_s {
+    int n;
+    rsgm_stream *members;   // not owned
+    cudaStream_t launch;    // the members' stream: the graph is launched there
+    cudaStream_t *cap;      // one capture stream per member
+    cudaEvent_t fork;
+    cudaEvent_t *join;
+    cudaGraphExec_t exec;
+    int device;
+};
+
+namespace {
+void destroy_group(rsgm_group g)
+{
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (int k = 0; k < g->n; ++k) {
+        if (g->cap && g->cap[k]) cudaStreamDestroy(g->cap[k]);
+        if (g->join && g->join[k]) cudaEventDestroy(g->join[k]);
+    }
+    if (g->fork) cudaEventDestroy(g->fork);
+    free(g->cap);
+    free(g->join);
+    free(g->members);
+    free(g);
+}
+}  // namespace
+
+extern "C" {
+
+int rsgm_group_create(rsgm_group *out, rsgm_stream *members, int32_t n)
+{
+    if (!out) return fail(RSGM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!members || n < 1 || n > 64) return fail(RSGM_ERR_INVALID_ARG, "a group has 1 to 64 members");
+    for (int k = 0; k < n; ++k) {
+        if (!members[k]) return fail(RSGM_ERR_INVALID_ARG, "NULL member");
+        if (members[k]->device != members[0]->device || members[k]->st != members[0]->st)
+            return fail(RSGM_ERR_INVALID_ARG, "group members must share one device and one CUDA stream");
+        for (int j = 0; j < k; ++j)
+            if (members[j] == members[k]) return fail(RSGM_ERR_INVALID_ARG, "a handle appears twice in the group");
+    }
+    DeviceGuard dg(members[0]->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the members' device");
+    rsgm_group g = (rsgm_group)calloc(1, sizeof(rsgm_group_s));
+    if (!g) return fail(RSGM_ERR_OOM, "host allocation failed");
+    g->n = n;
+    g->launch = members[0]->st;
+    g->device = members[0]->device;
+    g->members = (rsgm_stream *)calloc((size_t)n, sizeof(rsgm_stream));
+    g->cap = (cudaStream_t *)calloc((size_t)n, sizeof(cudaStream_t));
+    g->join = (cudaEvent_t *)calloc((size_t)n, sizeof(cudaEvent_t));
+    if (!g->members || !g->cap || !g->join) {
+        destroy_group(g);
+        return fail(RSGM_ERR_OOM, "host allocation failed");
+    }
+    memcpy(g->members, members, (size_t)n * sizeof(rsgm_stream));
+    cudaError_t e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&g->cap[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        destroy_group(g);
+        return cuda_fail(e, "group streams");
+    }
+    *out = g;
+    return RSGM_OK;
+}
+
+int rsgm_group_reduced_frame(rsgm_group g, const uint8_t *const *left, const uint8_t *const *right,
+                             const float *const *R, const float *const *t, const float *const *K,
+                             const float *baseline)
+{
+    if (!g || !left || !right || !R || !t || !K || !baseline)
+        return fail(RSGM_ERR_INVALID_ARG, "NULL group or argument array");
+    for (int k = 0; k < g->n; ++k) {
+        int rc = check_reduced_args(g->members[k], left[k], right[k], R[k], t[k], K[k], baseline[k]);
+        if (rc) return rc;
+        if (!is_device_pointer(left[k]) || !is_device_pointer(right[k]))
+            return fail(RSGM_ERR_INVALID_ARG, "group frames take device images");
+    }
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the group's device");
+    // Capture every member's frame on its own stream (forked from and joined
+    // back into the first), so that the graph runs them concurrently.
+    RSGM_CUDA(cudaStreamBeginCapture(g->cap[0], cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(g->fork, g->cap[0]);
+    for (int k = 1; k < g->n && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(g->cap[k], g->fork, 0);
+    int rc = e == cudaSuccess ? RSGM_OK : cuda_fail(e, "group fork");
+    for (int k = 0; k < g->n && rc == RSGM_OK; ++k) {
+        rsgm_stream m = g->members[k];
+        cudaStream_t saved = m->st;
+        m->st = g->cap[k];
+        m->capturing = true;
+        rc = enqueue_reduced(m, left[k], right[k], R[k], t[k], K[k], baseline[k]);
+        m->capturing = false;
+        m->st = saved;
+    }
+    for (int k = 1; k < g->n && rc == RSGM_OK; ++k) {
+        e = cudaEventRecord(g->join[k], g->cap[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap[0], g->join[k], 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "group join");
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(g->cap[0], &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    // Same launches every tick, new arguments: update the executable in place.
+    if (g->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g->exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
+    }
+    if (!g->exec && (e = cudaGraphInstantiate(&g->exec, graph, 0)) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        g->exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    e = cudaGraphLaunch(g->exec, g->launch);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return RSGM_OK;
+}
+
+int rsgm_group_destroy(rsgm_group g)
+{
+    if (!g) return RSGM_OK;
+    DeviceGuard dg(g->device);
+    cudaError_t e = cudaStreamSynchronize(g->launch);
+    destroy_group(g);
+    return e == cudaSuccess ? RSGM_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
 
 }  // extern "C"

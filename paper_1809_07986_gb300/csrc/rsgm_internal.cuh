@@ -108,7 +108,7 @@ cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStre
 // `lanes` lanes per path line, planes of `plane_bytes` (1 or 2) per cell.
 int lanes_per_line(int widest_narrow_window);
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         int lanes, int plane_bytes, int sm_count, cudaStream_t st);
+                         int lanes, int plane_bytes, int sm_count, int lines_override, cudaStream_t st);
 
 // Sum of the planes, winner-takes-all, Kalman correction and gate
 // (Sections 2.2-2.4).

@@ -1,0 +1,111 @@
+"""Mixed-resolution groups (several handles of different geometry, one CUDA
+graph launch per tick) and the schedule autotuner: results are the same,
+bit for bit, alone and in the mix, and the same whatever schedule the tuner
+picks; one member is also checked against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from parity_util import compare_stream, oracle_params, read_all
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_07986_gb300 import build
+    build.build()
+    import paper_1809_07986_gb300 as rs
+    return rs
+
+
+GEOMS = [  # (B, W, H, D, f)
+    (2, 160, 120, 32, 100.0),
+    (2, 300, 90, 64, 200.0),
+    (1, 200, 150, 96, 250.0),
+]
+
+
+def _inputs(nframes):
+    import synth
+    out = []
+    for gi, (B, W, H, D, f) in enumerate(GEOMS):
+        seqs = [synth.kitti_like_sequence(300 + 10 * gi + b, n_frames=nframes, width=W, height=H, f=f,
+                                          baseline=0.54) for b in range(B)]
+        st = lambda k: torch.stack([q[k] for q in seqs])
+        out.append(dict(L=st("left"), R=st("right"), Rm=st("R"), t=st("t"), K=seqs[0]["K"]))
+    return out
+
+
+def _params(rs, B, W, H, D):
+    return rs.rsgm_default_params(W, H, max_disp=D, radius=4, batch=B)
+
+
+def test_group_matches_members_run_alone(rs, orc):
+    nframes = 4
+    data = _inputs(nframes)
+    stream = torch.cuda.current_stream()
+    alone, grouped = [], []
+    for (B, W, H, D, f), x in zip(GEOMS, data):
+        alone.append(rs.Stream(_params(rs, B, W, H, D), stream))
+        grouped.append(rs.Stream(_params(rs, B, W, H, D), stream))
+    group = rs.rsgm_group_create([s.handle for s in grouped])
+    try:
+        for k in range(nframes):
+            L = [x["L"][:, k].cuda().contiguous() for x in data]
+            R = [x["R"][:, k].cuda().contiguous() for x in data]
+            if k == 0:
+                for s, l, r in zip(alone + grouped, L + L, R + R):
+                    s.full_frame(l, r)
+                continue
+            for s, x, l, r in zip(alone, data, L, R):
+                s.reduced_frame(l, r, x["Rm"][:, k].contiguous(), x["t"][:, k].contiguous(), x["K"], 0.54)
+            rs.rsgm_group_reduced_frame(group, L, R, [x["Rm"][:, k].contiguous() for x in data],
+                                        [x["t"][:, k].contiguous() for x in data], [x["K"] for x in data],
+                                        [0.54] * len(data))
+            if k == 2:   # tune the members' schedules in the middle of the sequence
+                for s in grouped:
+                    rs.rsgm_autotune(s.handle)
+            for a, b in zip(alone, grouped):
+                for u, v in zip(a.state(), b.state()):
+                    assert torch.equal(u, v), "frame %d" % k
+        # one member against the oracle on the last frame
+        g = read_all(rs, grouped[1])
+        B, W, H, D, f = GEOMS[1]
+        op = oracle_params(orc, _params(rs, B, W, H, D))
+        x = data[1]
+        for b in range(B):
+            st = None
+            for k in range(nframes):
+                if k == 0:
+                    o = orc.frame(op, x["L"][b, 0].numpy(), x["R"][b, 0].numpy())
+                else:
+                    o = orc.frame(op, x["L"][b, k].numpy(), x["R"][b, k].numpy(), state=st,
+                                  motion=(x["Rm"][b, k].numpy(), x["t"][b, k].numpy(), x["K"].numpy(), 0.54))
+                st = (o["d"], o["p"])
+            compare_stream(g, b, o, H, W)
+    finally:
+        rs.rsgm_group_destroy(group)
+        for s in alone + grouped:
+            s.close()
+
+
+def test_group_rejects_host_images_and_mixed_streams(rs):
+    P = rs.rsgm_default_params(64, 32, max_disp=16)
+    with rs.Stream(P) as a, rs.Stream(P, torch.cuda.Stream()) as b:
+        with pytest.raises(rs.RsgmError) as e:
+            rs.rsgm_group_create([a.handle, b.handle])
+        assert e.value.code == rs.RSGM_ERR_INVALID_ARG
+        z = torch.zeros(32, 64, dtype=torch.uint8, device="cuda")
+        a.full_frame(z, z)
+        g = rs.rsgm_group_create([a.handle])
+        try:
+            zh = torch.zeros(32, 64, dtype=torch.uint8)
+            K = torch.tensor([[30.0, 0, 31.5], [0, 30.0, 15.5], [0, 0, 1]])
+            with pytest.raises(rs.RsgmError) as e:
+                rs.rsgm_group_reduced_frame(g, [zh], [zh], [torch.eye(3)[None]], [torch.zeros(1, 3)], [K], [0.5])
+            assert e.value.code == rs.RSGM_ERR_INVALID_ARG
+        finally:
+            rs.rsgm_group_destroy(g)
