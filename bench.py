@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--radius", type=int, default=4)
     ap.add_argument("--mixed", action="store_true",
                     help="also time the mixed-resolution group (6x640x480/D64, 6x1242x375/D128, 4x1920x1080/D256)")
+    ap.add_argument("--serve", action="store_true",
+                    help="also run the request loop: 32 Poisson streams (10-30 Hz) of 640x480/1242x375/1920x1080")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-form, latency, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -274,6 +276,33 @@ def mixed_group(args, dev, stream):
             "graph_launches_per_tick": 1, "lines_per_warp_tuned": tuned}
 
 
+# ------------------------------------------------------------------ request loop
+
+def serving_loop(dev, nstreams=32, frames=20, budget_gb=48.0, seed=9):
+    """32 streams appear over one second, each a Poisson process at 10-30 Hz
+    of a resolution drawn from {640x480/D64, 1242x375/D128, 1920x1080/D256};
+    admission by device footprint under a budget; first frame full range."""
+    import numpy as np
+    import synth
+    from paper_1809_07986_gb300.serving import GpuBackend, StreamSpec, poisson_arrivals, serve
+    rng = np.random.default_rng(seed)
+    kinds = [(640, 480, 64, 400.0), (1242, 375, 128, 721.0), (1920, 1080, 256, 1000.0)]
+    specs, data = [], {}
+    for i in range(nstreams):
+        W_, H_, D_, f_ = kinds[int(rng.integers(0, 3))]
+        s = synth.kitti_like_sequence(9000 + i, n_frames=100, width=W_, height=H_, f=f_, baseline=BASE, device=dev,
+                                      render_frames=frames)
+        data[i] = dict(left=s["left"], right=s["right"], R=s["R"], t=s["t"], K=s["K"], baseline=BASE)
+        start = float(rng.uniform(0.0, 1.0))
+        specs.append(StreamSpec(i, W_, H_, D_, start, poisson_arrivals(rng, start, float(rng.uniform(10, 30)), frames)))
+    backend = GpuBackend(data, device=dev)
+    rep = serve(specs, backend, budget_bytes=int(budget_gb * 1e9))
+    out = rep.summary()
+    out.update(streams=nstreams, frames_per_stream=frames, budget_gb=budget_gb, order_ok=rep.order_ok,
+               arrival="Poisson 10-30 Hz per stream, streams appearing over 1 s")
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, rank, world, local_rank):
@@ -463,6 +492,8 @@ def run_ours(args, rank, world, local_rank):
 
         if args.mixed and rank == 0:
             result["mixed_group"] = mixed_group(args, dev, stream)
+        if args.serve and rank == 0:
+            result["serving"] = serving_loop(dev)
 
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)

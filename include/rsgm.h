@@ -115,6 +115,10 @@ int rsgm_default_params(rsgm_params *p, int32_t width, int32_t height);
  */
 int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream);
 
+/* Device bytes rsgm_init_stream allocates for these parameters (for
+ * admission control by memory footprint). */
+int rsgm_footprint(const rsgm_params *p, uint64_t *bytes);
+
 /*
  * The initial frame (Section 2.4, last paragraph: limits initially cover the
  * whole search space, i.e. conventional SGM).  Every pixel searches [0, D);

@@ -86,6 +86,7 @@ _P = ctypes.c_void_p
 SIGNATURES = {
     "rsgm_default_params": (ctypes.c_int, [ctypes.POINTER(rsgm_params), ctypes.c_int32, ctypes.c_int32]),
     "rsgm_init_stream": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(rsgm_params), _P]),
+    "rsgm_footprint": (ctypes.c_int, [ctypes.POINTER(rsgm_params), ctypes.POINTER(ctypes.c_uint64)]),
     "rsgm_full_frame": (ctypes.c_int, [_P, _P, _P]),
     "rsgm_reduced_frame": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_float]),
     "rsgm_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -182,6 +183,12 @@ def rsgm_default_params(width: int, height: int, **overrides) -> rsgm_params:
             raise AttributeError("rsgm_params has no field %r" % k)
         setattr(p, k, v)
     return p
+
+
+def rsgm_footprint(params: rsgm_params) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().rsgm_footprint(ctypes.byref(params), ctypes.byref(n)), "rsgm_footprint")
+    return n.value
 
 
 def rsgm_init_stream(params: rsgm_params, cuda_stream=None) -> int:

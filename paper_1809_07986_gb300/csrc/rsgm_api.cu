@@ -308,6 +308,22 @@ int rsgm_default_params(rsgm_params *p, int32_t width, int32_t height)
     return RSGM_OK;
 }
 
+int rsgm_footprint(const rsgm_params *p, uint64_t *bytes)
+{
+    if (!bytes) return fail(RSGM_ERR_INVALID_ARG, "bytes is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    const uint64_t n = (uint64_t)p->batch * p->width * p->height;
+    const uint64_t cells = n * (uint64_t)p->max_disp;
+    const int nbits = p->census_w * p->census_h - 1;
+    const uint64_t plane_bytes = nbits + p->P2 <= 255 ? 1 : 2;
+    const uint64_t stride = (cells + 15) / 16 * 16;
+    const uint64_t per_pixel = 2 + 16 + 8 + 8 + 8 + 4 + 1 + 4 + 8 + 2 + 1 + 4 + 4 + 4 + RSGM_MAX_WINDOW_SIZES;
+    *bytes = n * per_pixel + cells * (1 + 2) + 16 + stride * __builtin_popcount(p->path_mask) * plane_bytes +
+             (uint64_t)p->batch * p->height * 8 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32;
+    return RSGM_OK;
+}
+
 int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
 {
     if (!out) return fail(RSGM_ERR_INVALID_ARG, "out is NULL");
