@@ -267,12 +267,17 @@ int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t 
 
 /*
  * Schedule autotuner.  Times the aggregation kernel (Eq. 1) on the handle's
- * latest frame with each candidate number of path lines per warp and keeps
- * the fastest for later frames (written to *lines_per_warp if not NULL).
+ * latest frame with each candidate schedule -- 1, 2, 4, ... path lines per
+ * warp -- and keeps the fastest for later frames (written to *lines_per_warp
+ * if not NULL).
  * Results do not depend on the choice; only speed does.  Requires a
  * processed frame; synchronises.
  */
 int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp);
+
+/* Sets the aggregation schedule by hand: 0 = automatic, else path lines per
+ * warp (capped at what the lanes allow).  Results do not depend on it. */
+int rsgm_set_schedule(rsgm_stream s, int32_t lines_per_warp);
 
 /*
  * A group advances several handles of possibly different geometry by one

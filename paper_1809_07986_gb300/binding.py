@@ -101,6 +101,7 @@ SIGNATURES = {
     "rsgm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_window_offsets_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "rsgm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "rsgm_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rsgm_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32]),
     "rsgm_group_reduced_frame": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                                 ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
@@ -293,6 +294,10 @@ def rsgm_autotune(h: int) -> int:
     n = ctypes.c_int32()
     _check(lib().rsgm_autotune(h, ctypes.byref(n)), "rsgm_autotune")
     return n.value
+
+
+def rsgm_set_schedule(h: int, lines_per_warp: int):
+    _check(lib().rsgm_set_schedule(h, lines_per_warp), "rsgm_set_schedule")
 
 
 def rsgm_group_create(handles) -> int:

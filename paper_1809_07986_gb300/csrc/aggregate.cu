@@ -262,16 +262,23 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     plan.ndir = 0;
     plan.warp_begin[0] = 0;
     plan.lanes = lanes;
-    // Lines per warp: as many as the lanes allow (32 / lanes), fewer when the
-    // batch is small, so that the launch still fills every SM with 32 warps;
-    // a warp's steps run one after another, so small batches favour more,
-    // shorter-running warps.
+    // Lines per warp.  fill = lines per warp that would give every SM 32
+    // warps; about a quarter of it (measured on paper-shaped frames at 1, 8,
+    // 32 and 64 streams) balances a warp's sequential steps against the work
+    // its lines share per step.  Capped by the lanes (32 / lanes) and by the
+    // line buffers: those of 8 resident blocks stay within 168 KB, so that a
+    // third of the SM's 256 KB L1 still caches the cost and window loads (at
+    // D = 128, 12 lines per warp ran 10% slower than 10).
     long long total_lines = 0;
     for (int dir = 0; dir < 8; ++dir)
         if (path_mask & (1u << dir)) total_lines += (long long)g.B * lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H);
     const long long fill = total_lines / ((long long)(sm_count > 0 ? sm_count : 152) * 32);
-    plan.lines_per_warp = (int)(fill < 1 ? 1 : (fill > 32 / lanes ? 32 / lanes : fill));
-    if (lines_override > 0) plan.lines_per_warp = lines_override < 32 / lanes ? lines_override : 32 / lanes;
+    const long long smem_cap = (168LL * 1024 / 8) / ((long long)kWarpsPerBlock * line_stride(g.D) * 2);
+    long long most = 32 / lanes;
+    if (smem_cap < most) most = smem_cap < 1 ? 1 : smem_cap;
+    const long long pick = (fill + 2) / 4;
+    plan.lines_per_warp = (int)(pick < 1 ? 1 : (pick > most ? most : pick));
+    if (lines_override > 0) plan.lines_per_warp = (int)(lines_override < 32 / lanes ? lines_override : 32 / lanes);
     const int lines_per_warp = plan.lines_per_warp;
     for (int k = 0; k < 8; ++k) {
         const int dir = order[k];

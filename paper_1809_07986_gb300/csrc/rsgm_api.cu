@@ -672,6 +672,14 @@ const char *rsgm_last_error(void) { return g_last_error; }
 
 // ------------------------------------------------------------------ groups
 
+int rsgm_set_schedule(rsgm_stream s, int32_t lines_per_warp)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    if (lines_per_warp < 0 || lines_per_warp > 32) return fail(RSGM_ERR_INVALID_ARG, "lines_per_warp in [0, 32]");
+    s->tuned_lines = lines_per_warp;
+    return RSGM_OK;
+}
+
 int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
 {
     if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
@@ -684,13 +692,18 @@ int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
         cudaEventDestroy(e0);
         return fail(RSGM_ERR_CUDA, "cudaEventCreate");
     }
+    // candidates: 1, 2, 4, ... up to 32 / lanes path lines per warp
+    int cands[16], nc = 0;
     const int most = 32 / s->lanes;
+    for (int c = 1; c < most; c *= 2) cands[nc++] = c;
+    cands[nc++] = most;
     int best = 0;
     float best_ms = 0.0f;
     int rc = RSGM_OK;
     // Every candidate computes the same planes (each schedule is exact), so
     // re-running the aggregation on the last frame's costs changes nothing.
-    for (int cand = 1; cand <= most && rc == RSGM_OK; cand = cand < most && cand * 2 > most ? most : cand * 2) {
+    for (int ci = 0; ci < nc && rc == RSGM_OK; ++ci) {
+        const int cand = cands[ci];
         float ms = 1e30f;
         for (int rep = 0; rep < 3 && rc == RSGM_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, s->st);
@@ -708,7 +721,6 @@ int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
             best = cand;
             best_ms = ms;
         }
-        if (cand == most) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -107,6 +107,7 @@ cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStre
 // Aggregation, Eq. 1 (Section 2.2): every enabled direction in one launch,
 // `lanes` lanes per path line, planes of `plane_bytes` (1 or 2) per cell.
 int lanes_per_line(int widest_narrow_window);
+// lines_override: 0 = automatic, else path lines per warp.
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
                          int lanes, int plane_bytes, int sm_count, int lines_override, cudaStream_t st);
 

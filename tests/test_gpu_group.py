@@ -109,3 +109,37 @@ def test_group_rejects_host_images_and_mixed_streams(rs):
             assert e.value.code == rs.RSGM_ERR_INVALID_ARG
         finally:
             rs.rsgm_group_destroy(g)
+
+
+@pytest.mark.parametrize("radius", [2, 4, 8])
+def test_every_schedule_gives_the_same_aggregation(rs, radius):
+    # Eq. 1 is exact in integers, so S and the state must not depend on how
+    # many path lines a warp carries; oversized requests are capped.
+    B, W, H, D, f = 3, 240, 100, 64, 150.0
+    import synth
+    seqs = [synth.kitti_like_sequence(700 + b, n_frames=3, width=W, height=H, f=f, baseline=0.54) for b in range(B)]
+    st = lambda k: torch.stack([q[k] for q in seqs])
+    L, R, Rm, t, K = st("left"), st("right"), st("R"), st("t"), seqs[0]["K"]
+    P = rs.rsgm_default_params(W, H, max_disp=D, radius=radius, batch=B)
+    results = {}
+    for sched in [0, 1, 2, 3, 5, 7, 16, 32]:
+        with rs.Stream(P) as s:
+            rs.rsgm_set_schedule(s.handle, sched)
+            s.full_frame(L[:, 0].cuda().contiguous(), R[:, 0].cuda().contiguous())
+            for k in (1, 2):
+                s.reduced_frame(L[:, k].cuda().contiguous(), R[:, k].cuda().contiguous(), Rm[:, k].contiguous(),
+                                t[:, k].contiguous(), K, 0.54)
+            results[sched] = [s.read(rs.RSGM_BUF_AGGREGATED, torch.int16)] + [x.cpu() for x in s.state()]
+    base = results[0]
+    for sched, got in results.items():
+        for u, v in zip(base, got):
+            assert torch.equal(u, v), "schedule %d" % sched
+
+
+def test_set_schedule_rejects_out_of_range(rs):
+    P = rs.rsgm_default_params(64, 32, max_disp=16)
+    with rs.Stream(P) as s:
+        for bad in (-1, 33):
+            with pytest.raises(rs.RsgmError) as e:
+                rs.rsgm_set_schedule(s.handle, bad)
+            assert e.value.code == rs.RSGM_ERR_INVALID_ARG
