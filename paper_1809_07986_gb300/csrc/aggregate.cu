@@ -88,8 +88,7 @@ __device__ __forceinline__ unsigned cells(const uint8_t *cst, T *pl, const uint1
 // Walks NS = 32 / G path lines of direction (dx, dy) with one warp.
 //
 // Narrow pixels (window width <= G * kV) are handled by the line's segment of
-// G lanes, kV consecutive cells per lane; the segment's minimum comes from
-// one reduction over the segment's lane mask.  Wide pixels (the full-range
+// G lanes, kV consecutive cells per lane.  Wide pixels (the full-range
 // windows of discontinuity resets and pixels without a prediction) are
 // handled afterwards by the whole warp, one pixel at a time, kVW cells per
 // lane.  The predecessor's losses sit in a per-line shared buffer indexed by
@@ -98,6 +97,12 @@ __device__ __forceinline__ unsigned cells(const uint8_t *cst, T *pl, const uint1
 // cache).  Metadata is fetched two pixels ahead, narrow pixels' costs one
 // pixel ahead.  The lines' buffers are padded apart by three banks: adjacent
 // lines read similar disparities at the same time.
+//
+// Loads and the first chunk of a wide pixel run without conditions (the
+// cost volume is padded for the over-reads; cells outside a window are
+// neither stored nor counted): guarded loads cost more issue slots than the
+// loads themselves.  The segment minimum comes from shuffles: a masked
+// reduction with a different mask per segment runs once per segment.
 template <typename T>
 __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long line0,
                                       const uint8_t *__restrict__ cost, T *__restrict__ plane,
@@ -105,13 +110,13 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
                                       uint16_t *wbuf)
 {
     const int lane = threadIdx.x & 31;
-    const int seg = lane / G;  // == NS for the idle lanes above NS * G
+    const int seg = lane / G;  // >= NS for the idle lanes above NS * G
     const int sl = lane - seg * G;
     const int kb = sl * kV;    // first window cell of this lane (narrow pixels)
     const int cap_n = G * kV;  // widest narrow window
-    const unsigned low = G == 32 ? kFull : (1u << G) - 1u;
-    const unsigned segmask = seg < NS ? low << (seg * G) : ~((NS * G == 32) ? kFull : (1u << (NS * G)) - 1u);
     const int nl = lines_per_stream(dx, dy, g.W, g.H);
+    // source lanes of the segment's other values (segments of at most 4 lanes)
+    const int src1 = seg * G + (sl + 1) % G, src2 = seg * G + (sl + 2) % G, src3 = seg * G + (sl + 3) % G;
     const long long line = line0 + seg;
     int n = 0;
     const uint2 *mp = meta;
@@ -130,22 +135,15 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
     uint2 mc = n > 0 ? mp[0] : make_uint2(0u, 0u);
     uint2 mn = n > 1 ? mp[step] : make_uint2(0u, 0u);
     uint8_t cc[kV];
-    {
-        const int w0 = (int)(mc.y >> 16);
 #pragma unroll
-        for (int v = 0; v < kV; ++v) cc[v] = (n > 0 && kb + v < w0 && w0 <= cap_n) ? cost[mc.x + kb + v] : 0;
-    }
+    for (int v = 0; v < kV; ++v) cc[v] = cost[mc.x + kb + v];
     int plo = 0, pw = 0, pmin = 0;
     for (int i = 0; i < nmax; ++i) {
         mp += step;
         const uint2 mnn = (i + 2 < n) ? mp[step] : make_uint2(0u, 0u);
         uint8_t cn[kV];
-        {
-            const int wn = (int)(mn.y >> 16);
 #pragma unroll
-            for (int v = 0; v < kV; ++v)
-                cn[v] = (i + 1 < n && kb + v < wn && wn <= cap_n) ? cost[mn.x + kb + v] : 0;
-        }
+        for (int v = 0; v < kV; ++v) cn[v] = cost[mn.x + kb + v];
         const unsigned o = mc.x;
         const int lo = (int)(mc.y & 0xFFFFu);
         const int w = i < n ? (int)(mc.y >> 16) : 0;
@@ -156,7 +154,21 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
         if (w <= cap_n && kb < w)
             lmin = cells<kV, T>(cc, plane + o + kb, sel ? bufA : bufB, sel ? bufB : bufA, lo + kb, kb, w, plo, pw,
                                 cap, pmin, P1);
-        lmin = __reduce_min_sync(segmask, lmin);
+        if (G == 32) {
+            lmin = __reduce_min_sync(kFull, lmin);
+        } else if (G <= 4) {
+            // every lane gathers its segment's other G - 1 values
+            const unsigned l0 = lmin;
+            lmin = min(lmin, __shfl_sync(kFull, l0, src1));
+            if (G > 2) lmin = min(lmin, __shfl_sync(kFull, l0, src2));
+            if (G > 3) lmin = min(lmin, __shfl_sync(kFull, l0, src3));
+        } else {
+            for (int off = 1; off < G; off <<= 1) {
+                const unsigned y = __shfl_down_sync(kFull, lmin, off);
+                if (sl + off < G) lmin = min(lmin, y);
+            }
+            lmin = __shfl_sync(kFull, lmin, seg * G);
+        }
 
         // wide pixels: the whole warp, one pixel at a time
         unsigned wide = __ballot_sync(kFull, seg < NS && sl == 0 && w > cap_n);
@@ -173,13 +185,15 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
             const int cap2 = i == 0 ? 0 : pmin2 + P2;
             uint16_t *b2 = wbuf + s2 * line_stride(g.D);
             unsigned m2 = kInf;
-            for (int k0 = lane * kVW; k0 < w2; k0 += 32 * kVW) {
+            int k0 = lane * kVW;
+            do {
                 uint8_t c4[kVW];
 #pragma unroll
-                for (int v = 0; v < kVW; ++v) c4[v] = k0 + v < w2 ? cost[o2 + k0 + v] : 0;
+                for (int v = 0; v < kVW; ++v) c4[v] = cost[o2 + k0 + v];
                 m2 = min(m2, cells<kVW, T>(c4, plane + o2 + k0, b2 + (sel ^ 1) * g.D, b2 + sel * g.D, lo2 + k0, k0,
                                            w2, plo2, pw2, cap2, pmin2, P1));
-            }
+                k0 += 32 * kVW;
+            } while (k0 < w2);
             m2 = __reduce_min_sync(kFull, m2);
             if (seg == s2) lmin = m2;
         }

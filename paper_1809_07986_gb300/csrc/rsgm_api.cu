@@ -319,7 +319,7 @@ int rsgm_footprint(const rsgm_params *p, uint64_t *bytes)
     const uint64_t plane_bytes = nbits + p->P2 <= 255 ? 1 : 2;
     const uint64_t stride = (cells + 15) / 16 * 16;
     const uint64_t per_pixel = 2 + 16 + 8 + 8 + 8 + 4 + 1 + 4 + 8 + 2 + 1 + 4 + 4 + 4 + RSGM_MAX_WINDOW_SIZES;
-    *bytes = n * per_pixel + cells * (1 + 2) + 16 + stride * __builtin_popcount(p->path_mask) * plane_bytes +
+    *bytes = n * per_pixel + cells * (1 + 2) + 128 + stride * __builtin_popcount(p->path_mask) * plane_bytes +
              (uint64_t)p->batch * p->height * 8 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32;
     return RSGM_OK;
 }
@@ -369,7 +369,7 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc(&b.p_pred, n, all, nall)) || (rc = alloc(&b.win, n, all, nall)) ||
         (rc = alloc(&b.cls, n, all, nall)) || (rc = alloc(&b.inrow, n, all, nall)) ||
         (rc = alloc(&b.meta, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
-        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells + 16, all, nall)) ||  // + the aligned-word over-read of staged copies
+        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells + 128, all, nall)) ||  // + the path sweeps' unguarded over-reads (< 128 B)
         (rc = alloc((uint8_t **)&b.planes, (size_t)plane_stride(s->g) * s->nplanes * s->plane_bytes, all, nall)) ||
         (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
         (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
