@@ -138,6 +138,9 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
 #pragma unroll
     for (int v = 0; v < kV; ++v) cc[v] = cost[mc.x + kb + v];
     int plo = 0, pw = 0, pmin = 0;
+    // unrolled by two so that the fetched-ahead registers swap roles instead
+    // of being copied (a copy would wait for the fetch to land)
+#pragma unroll 2
     for (int i = 0; i < nmax; ++i) {
         mp += step;
         const uint2 mnn = (i + 2 < n) ? mp[step] : make_uint2(0u, 0u);

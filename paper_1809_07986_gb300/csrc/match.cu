@@ -55,13 +55,15 @@ __global__ void __launch_bounds__(kTileX *kTileY) k_census(const uint8_t *__rest
 }
 
 constexpr int kCostWarps = 4;
+constexpr int kLaneCells = 16;  // windows up to this width are filled by their own lane
 
 // K3: one warp per 32 consecutive pixels.  Each lane finalises one pixel's
-// metadata (first cell = row base + in-row prefix, window); the pixels' cells
-// form one contiguous span (raster-order prefix sum), which the warp then
-// walks 32 cells at a time: a lane finds its cell's pixel by a binary search
-// over the lanes' first cells and writes C(p, d) = popcount(cL(x,y) ^
-// cR(x-d,y)); a match left of the image costs every census bit.
+// metadata (first cell = row base + in-row prefix, window) and writes its
+// window's costs C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)), a match left of the
+// image costing every census bit.  Narrow windows (up to kLaneCells cells)
+// are filled by their own lane (neighbouring lanes read overlapping right
+// census words, which the L1 serves); wider ones by the whole warp, one pixel
+// at a time, 32 consecutive cells per pass.
 __global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long long *__restrict__ cen_l,
                                                          const unsigned long long *__restrict__ cen_r,
                                                          const uint32_t *__restrict__ win,
@@ -73,13 +75,13 @@ __global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long lo
     const int lane = threadIdx.x & 31;
     const long long gi0 = ((long long)blockIdx.x * kCostWarps + (threadIdx.x >> 5)) * 32;
     if (gi0 >= g.NPIX) return;  // uniform per warp
-    const int nvalid = (int)min(32LL, g.NPIX - gi0);
     const long long gi = gi0 + lane;
+    const bool valid = gi < g.NPIX;
     unsigned o = 0, wv = 0;
     int x = 0;
     long long row = 0;
     unsigned long long cl = 0;
-    if (lane < nvalid) {
+    if (valid) {
         row = gi / g.W;
         x = (int)(gi - row * g.W);
         o = row_base[row] + inrow[gi];
@@ -87,27 +89,27 @@ __global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long lo
         meta[gi] = make_uint2(o, wv);
         cl = cen_l[gi];
     }
-    const unsigned span0 = __shfl_sync(0xffffffffu, o, 0);
-    const unsigned span1 = __shfl_sync(0xffffffffu, o + (wv >> 16), nvalid - 1);
-    for (unsigned base = span0; base < span1; base += 32) {  // uniform trip count: shuffles inside
-        const unsigned c = base + lane;
-        // pixel of cell c: the last lane whose first cell is <= c
-        int j = 0;
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const int t = j + s;
-            const unsigned ot = __shfl_sync(0xffffffffu, o, t & 31);
-            if (t < nvalid && ot <= c) j = t;
+    const int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
+    const unsigned long long *cr = cen_r + row * g.W;
+    if (valid && w <= kLaneCells) {
+        for (int k = 0; k < w; ++k) {
+            const int xr = x - lo - k;
+            cost[o + k] = (uint8_t)(xr >= 0 ? __popcll(cl ^ cr[xr]) : nbits);
         }
-        const unsigned oj = __shfl_sync(0xffffffffu, o, j);
-        const unsigned wj = __shfl_sync(0xffffffffu, wv, j);
-        const int xj = __shfl_sync(0xffffffffu, x, j);
-        const long long rj = __shfl_sync(0xffffffffu, row, j);
-        const unsigned long long clj = __shfl_sync(0xffffffffu, cl, j);
-        if (c < span1) {
-            const int d = (int)(wj & 0xFFFFu) + (int)(c - oj);
-            const int xr = xj - d;
-            cost[c] = (uint8_t)(xr >= 0 ? __popcll(clj ^ cen_r[rj * g.W + xr]) : nbits);
+    }
+    unsigned wide = __ballot_sync(0xffffffffu, valid && w > kLaneCells);
+    while (wide) {
+        const int src = __ffs(wide) - 1;
+        wide &= wide - 1;
+        const unsigned o2 = __shfl_sync(0xffffffffu, o, src);
+        const int w2 = __shfl_sync(0xffffffffu, w, src);
+        const int xl = __shfl_sync(0xffffffffu, x - lo, src);  // right-image column of the window's first cell
+        const long long r2 = __shfl_sync(0xffffffffu, row, src);
+        const unsigned long long cl2 = __shfl_sync(0xffffffffu, cl, src);
+        const unsigned long long *cr2 = cen_r + r2 * g.W;
+        for (int k = lane; k < w2; k += 32) {
+            const int xr = xl - k;
+            cost[o2 + k] = (uint8_t)(xr >= 0 ? __popcll(cl2 ^ cr2[xr]) : nbits);
         }
     }
 }

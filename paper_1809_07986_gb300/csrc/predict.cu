@@ -55,25 +55,24 @@ __global__ void __launch_bounds__(256) k_splat(const float *__restrict__ d,
     atomicMax(key + tgt, k);
 }
 
-// Decodes the splat that won pixel t of a stream and evaluates Eq. 3-4 for it.
-__device__ __forceinline__ bool winner(const unsigned long long *__restrict__ key,
-                                       const float *__restrict__ d, const float *__restrict__ p,
-                                       long long base, long long t, float q, float &dd, float &pp)
+// Eq. 3-4 for the splat encoded in key k (k != kEmpty) of a stream at `base`.
+__device__ __forceinline__ void winner(unsigned long long k, const float *__restrict__ d,
+                                       const float *__restrict__ p, long long base, float q, float &dd,
+                                       float &pp)
 {
-    unsigned long long k = key[base + t];
-    if (k == kEmpty) return false;
     float dn = __uint_as_float((unsigned)(k >> 32));
     unsigned src = 0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull);
     float ds = d[base + src], ps = p[base + src];
     float phi = fdiv(dn, ds);                        // Eq. 3
     pp = fadd(fmul(fmul(phi, phi), ps), q);          // Eq. 4
     dd = dn;
-    return true;
 }
 
 // K1b: prediction per target pixel, with zoom holes (no point landed) filled
 // from two known horizontal or two known vertical neighbours (both pairs:
-// average of four).  Unknown pixels get d_pred = -1.
+// average of four).  Unknown pixels get d_pred = -1.  The pixel's and its
+// four neighbours' keys are fetched together, then the sources they name, so
+// that a hole costs two dependent fetches rather than up to ten.
 __global__ void __launch_bounds__(256) k_gather_fill(const unsigned long long *__restrict__ key,
                                                      const float *__restrict__ d,
                                                      const float *__restrict__ p,
@@ -86,17 +85,37 @@ __global__ void __launch_bounds__(256) k_gather_fill(const unsigned long long *_
     long long base = (long long)b * g.HW;
     int s = (int)(gi - base);
     int y = s / g.W, x = s - y * g.W;
+    const unsigned long long k0 = key[gi];
+    const bool hx = x > 0 && x < g.W - 1, hy = y > 0 && y < g.H - 1;
+    unsigned long long kl = kEmpty, kr = kEmpty, ku = kEmpty, kd = kEmpty;
+    if (k0 == kEmpty) {
+        if (hx) {
+            kl = key[gi - 1];
+            kr = key[gi + 1];
+        }
+        if (hy) {
+            ku = key[gi - g.W];
+            kd = key[gi + g.W];
+        }
+    }
     float dd, pp;
-    if (winner(key, d, p, base, s, q, dd, pp)) {
+    if (k0 != kEmpty) {
+        winner(k0, d, p, base, q, dd, pp);
         d_pred[gi] = dd;
         p_pred[gi] = pp;
         return;
     }
     float dl = 0, pl = 0, dr = 0, pr = 0, du = 0, pu = 0, dw = 0, pw = 0;
-    bool h = x > 0 && x < g.W - 1 && winner(key, d, p, base, s - 1, q, dl, pl) &&
-             winner(key, d, p, base, s + 1, q, dr, pr);
-    bool v = y > 0 && y < g.H - 1 && winner(key, d, p, base, s - g.W, q, du, pu) &&
-             winner(key, d, p, base, s + g.W, q, dw, pw);
+    const bool h = kl != kEmpty && kr != kEmpty;
+    const bool v = ku != kEmpty && kd != kEmpty;
+    if (h) {
+        winner(kl, d, p, base, q, dl, pl);
+        winner(kr, d, p, base, q, dr, pr);
+    }
+    if (v) {
+        winner(ku, d, p, base, q, du, pu);
+        winner(kd, d, p, base, q, dw, pw);
+    }
     if (h && v) {
         d_pred[gi] = fmul(fadd(fadd(dl, dr), fadd(du, dw)), 0.25f);
         p_pred[gi] = fmul(fadd(fadd(pl, pr), fadd(pu, pw)), 0.25f);
@@ -144,75 +163,94 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned &t
     return res;
 }
 
-// K1c: one block per image row.  Discontinuity reset (a known pixel with a
-// known 4-neighbour more than tau_disc away keeps d but takes p_reset and the
-// full window), the search window, the in-row exclusive prefix sum of the
-// widths, the row total; also clears the splat keys for the next frame.
-__global__ void __launch_bounds__(256) k_window(float *__restrict__ d_pred, float *__restrict__ p_pred,
+constexpr int kWinPer = 4;           // pixels per thread and tile for the in-row scan
+constexpr int kWinTile = 256 * kWinPer;
+
+// K1c: one block per image row, walking the row in tiles of kWinTile pixels.
+// A tile's predicted disparities and those of the rows above and below
+// (with a one-pixel halo; -1, "unknown", outside the image) are staged in
+// shared memory with coalesced loads.  Then per pixel: discontinuity reset (a
+// known pixel with a known 4-neighbour more than tau_disc away keeps d but
+// takes p_reset and the full window), the search window, and the splat key
+// cleared for the next frame; then the in-row exclusive prefix sum of the
+// widths (carried across tiles) and the row total.
+__global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred, float *__restrict__ p_pred,
                                                 uint32_t *__restrict__ win, uint8_t *__restrict__ cls,
                                                 uint32_t *__restrict__ inrow,
                                                 uint32_t *__restrict__ row_total,
                                                 unsigned long long *__restrict__ key, Geometry g,
                                                 FrameParams fp)
 {
+    __shared__ float sd[3][kWinTile + 2];  // rows y-1, y, y+1; column x0 - 1 + i at index i
+    __shared__ unsigned sw[kWinTile];
     __shared__ unsigned total;
-    int row = blockIdx.x;  // b * H + y
-    int y = row % g.H;
-    long long rbase = (long long)row * g.W;
-    int chunk = (g.W + blockDim.x - 1) / blockDim.x;
-    int x0 = threadIdx.x * chunk;
-    int x1 = min(g.W, x0 + chunk);
-    unsigned local = 0;
-    for (int x = x0; x < x1; ++x) {
-        long long gi = rbase + x;
-        float dc = d_pred[gi];
-        int lo = 0, w = g.D;
-        uint8_t c = 2;
-        if (dc >= 0.0f) {
-            bool reset = false;
-            float dn;
-            if (x > 0 && (dn = d_pred[gi - 1]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
-            if (x < g.W - 1 && (dn = d_pred[gi + 1]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
-            if (y > 0 && (dn = d_pred[gi - g.W]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
-            if (y < g.H - 1 && (dn = d_pred[gi + g.W]) >= 0.0f && fabsf(fsub(dn, dc)) > fp.tau_disc) reset = true;
-            if (reset) {
-                c = 1;
-            } else {
-                c = 0;
-                if (fp.radius_mode != RSGM_RADIUS_FULL) {
-                    int h;
-                    if (fp.radius_mode == RSGM_RADIUS_VARIANCE) {
-                        float cp = ceilf(p_pred[gi]);
-                        h = cp < 1.0f ? 1 : (cp > (float)g.D ? g.D : (int)cp);
-                    } else {
-                        h = fp.radius;
+    const int row = blockIdx.x;  // b * H + y
+    const int y = row % g.H;
+    const long long rbase = (long long)row * g.W;
+    unsigned carry = 0;
+    for (int x0 = 0; x0 < g.W; x0 += kWinTile) {
+        const int n = min(kWinTile, g.W - x0);
+        for (int i = threadIdx.x; i < n + 2; i += blockDim.x) {
+            const int x = x0 - 1 + i;
+            const bool in = x >= 0 && x < g.W;
+            sd[0][i] = in && y > 0 ? d_pred[rbase - g.W + x] : -1.0f;
+            sd[1][i] = in ? d_pred[rbase + x] : -1.0f;
+            sd[2][i] = in && y < g.H - 1 ? d_pred[rbase + g.W + x] : -1.0f;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const long long gi = rbase + x0 + i;
+            const float dc = sd[1][i + 1];
+            int lo = 0, w = g.D;
+            uint8_t c = 2;
+            if (dc >= 0.0f) {
+                const float nb[4] = {sd[1][i], sd[1][i + 2], sd[0][i + 1], sd[2][i + 1]};
+                bool reset = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (nb[k] >= 0.0f && fabsf(fsub(nb[k], dc)) > fp.tau_disc) reset = true;
+                if (reset) {
+                    c = 1;
+                    p_pred[gi] = fp.p_reset;
+                } else {
+                    c = 0;
+                    if (fp.radius_mode != RSGM_RADIUS_FULL) {
+                        int h;
+                        if (fp.radius_mode == RSGM_RADIUS_VARIANCE) {
+                            float cp = ceilf(p_pred[gi]);
+                            h = cp < 1.0f ? 1 : (cp > (float)g.D ? g.D : (int)cp);
+                        } else {
+                            h = fp.radius;
+                        }
+                        float cf = floorf(fadd(dc, 0.5f));
+                        int cc = cf < 0.0f ? 0 : (cf > (float)(g.D - 1) ? g.D - 1 : (int)cf);
+                        lo = max(0, cc - h);
+                        int hi = min(g.D - 1, cc + h);
+                        w = hi - lo + 1;
                     }
-                    float cf = floorf(fadd(dc, 0.5f));
-                    int cc = cf < 0.0f ? 0 : (cf > (float)(g.D - 1) ? g.D - 1 : (int)cf);
-                    lo = max(0, cc - h);
-                    int hi = min(g.D - 1, cc + h);
-                    w = hi - lo + 1;
                 }
             }
+            win[gi] = (uint32_t)lo | ((uint32_t)w << 16);
+            cls[gi] = c;
+            key[gi] = 0ull;
+            sw[i] = (unsigned)w;
         }
-        win[gi] = (uint32_t)lo | ((uint32_t)w << 16);
-        cls[gi] = c;
-        local += (unsigned)w;
+        __syncthreads();
+        const int j0 = threadIdx.x * kWinPer, j1 = min(j0 + kWinPer, n);
+        unsigned local = 0;
+        for (int j = j0; j < j1; ++j) local += sw[j];
+        unsigned pre = block_exclusive_scan(local, total) + carry;
+        for (int j = j0; j < j1; ++j) {
+            const unsigned wv = sw[j];
+            sw[j] = pre;
+            pre += wv;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) inrow[rbase + x0 + i] = sw[i];
+        carry += total;
+        __syncthreads();  // the next tile reuses sd, sw and total
     }
-    // The reset variance is written only after every neighbour read of this
-    // row's d_pred (p_pred is not read by neighbours).
-    for (int x = x0; x < x1; ++x) {
-        long long gi = rbase + x;
-        if (cls[gi] == 1) p_pred[gi] = fp.p_reset;
-        key[gi] = 0ull;
-    }
-    unsigned pre = block_exclusive_scan(local, total);
-    for (int x = x0; x < x1; ++x) {
-        long long gi = rbase + x;
-        inrow[gi] = pre;
-        pre += win[gi] >> 16;
-    }
-    if (threadIdx.x == 0) row_total[row] = total;
+    if (threadIdx.x == 0) row_total[row] = carry;
 }
 
 // Initial frame: every pixel searches [0, D) and has no prediction.

@@ -13,6 +13,8 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b)
 
 constexpr int kUpdWarps = 4;
 constexpr int kStageCells = 1024;  // per-warp staging of S; larger spans read S from global memory
+constexpr int kLaneScan = 16;      // unstaged windows up to this width are scanned by their own lane
+constexpr unsigned kFull = 0xffffffffu;
 
 // S = sum of the direction planes over the cells [c0, c1), written to S and to
 // the warp's staging buffer (indexed from c0).  8-bit planes are read four
@@ -80,8 +82,11 @@ __device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, 
 // span of the ragged volume (offsets are a raster-order prefix sum), so the
 // warp first sums the direction planes cell by cell with coalesced loads,
 // S(p,d) = sum_r L_r(p,d) (Section 2.2), writes S and, for spans of up to
-// kStageCells cells, stages it in shared memory; then each lane takes one pixel: d_int = first minimum of S over the
-// window; with both neighbours inside the window and den = S- - 2 S0 + S+ > 0
+// kStageCells cells, stages it in shared memory.  d_int = first minimum of S
+// over the window: each lane scans its own pixel's window in the staged copy
+// or, when S stays in global memory, a window of up to kLaneScan cells; wider
+// unstaged windows are scanned by the whole warp with coalesced loads, one
+// pixel at a time, as a minimum of (S << 16 | k) keys.  With both neighbours inside the window and den = S- - 2 S0 + S+ > 0
 // the measurement is d_int + (S- - S+) / (2 den).  Pixels without a
 // prediction take the measurement (d = d_z, p = r).  Otherwise
 // nu = d_z - d_pred; if nu^2 > gamma (p_pred + r) the pixel is flagged and
@@ -114,17 +119,37 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     uint16_t *stage = staged ? sS + warp * kStageCells : nullptr;
     sum_planes(planes, plane_stride, nplanes, span0, last_end, S, stage, lane);
     __syncwarp();  // S (shared or global) complete for the warp
-    if (!valid) return;
     const uint16_t *s = staged ? stage + (m.x - span0) : S + m.x;
     int best = 0;
-    unsigned bs = s[0];
-    for (int k = 1; k < w; ++k) {
-        const unsigned v = s[k];
-        if (v < bs) {
-            bs = v;
-            best = k;
+    unsigned bs = 0;
+    if (valid && (staged || w <= kLaneScan)) {
+        bs = s[0];
+        for (int k = 1; k < w; ++k) {
+            const unsigned v = s[k];
+            if (v < bs) {
+                bs = v;
+                best = k;
+            }
         }
     }
+    if (!staged) {
+        unsigned wide = __ballot_sync(kFull, valid && w > kLaneScan);
+        while (wide) {
+            const int src = __ffs(wide) - 1;
+            wide &= wide - 1;
+            const unsigned off = __shfl_sync(kFull, m.x, src);
+            const int ww = __shfl_sync(kFull, w, src);
+            const uint16_t *s2 = S + off;
+            unsigned key = 0xFFFFFFFFu;  // S in the high half, k in the low: the first minimum wins
+            for (int k = lane; k < ww; k += 32) key = min(key, ((unsigned)s2[k] << 16) | (unsigned)k);
+            key = __reduce_min_sync(kFull, key);
+            if (lane == src) {
+                bs = key >> 16;
+                best = (int)(key & 0xFFFFu);
+            }
+        }
+    }
+    if (!valid) return;
     int di = lo + best;
     float dz = (float)di;
     if (best >= 1 && best + 1 < w) {
