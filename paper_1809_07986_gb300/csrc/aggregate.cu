@@ -103,12 +103,14 @@ __device__ __forceinline__ unsigned cells(const uint8_t *cst, T *pl, const uint1
 // neither stored nor counted): guarded loads cost more issue slots than the
 // loads themselves.  The segment minimum comes from shuffles: a masked
 // reduction with a different mask per segment runs once per segment.
-template <typename T>
-__device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long line0,
+// GT > 0 fixes the lanes per line G at compile time; 0 takes G_rt.
+template <typename T, int GT>
+__device__ __forceinline__ void sweep(int dx, int dy, int G_rt, int NS, long long line0,
                                       const uint8_t *__restrict__ cost, T *__restrict__ plane,
                                       const uint2 *__restrict__ meta, const Geometry &g, int P1, int P2,
                                       uint16_t *wbuf)
 {
+    const int G = GT > 0 ? GT : G_rt;
     const int lane = threadIdx.x & 31;
     const int seg = lane / G;  // >= NS for the idle lanes above NS * G
     const int sl = lane - seg * G;
@@ -215,7 +217,7 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G, int NS, long long l
 __constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 __constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
-template <typename T>
+template <typename T, int GT>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_paths(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
             const __grid_constant__ PathPlan plan)
@@ -230,23 +232,37 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     uint16_t *wbuf = smem + warp * plan.lines_per_warp * line_stride(plan.g.D);
     T *plane = planes + (long long)plan.plane_of[s] * plan.plane_stride;
     const int dir = plan.dir[s];
-    sweep<T>(kDX[dir], kDY[dir], plan.lanes, plan.lines_per_warp, line0, cost, plane, meta, plan.g, plan.P1,
+    sweep<T, GT>(kDX[dir], kDY[dir], plan.lanes, plan.lines_per_warp, line0, cost, plane, meta, plan.g, plan.P1,
              plan.P2, wbuf);
 }
 
-template <typename T>
-cudaError_t launch_t(const Buffers &b, const PathPlan &plan, cudaStream_t st)
+template <typename T, int GT>
+cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
 {
     const long long warps = plan.warp_begin[plan.ndir];
     if (warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
     const size_t smem = (size_t)kWarpsPerBlock * plan.lines_per_warp * line_stride(plan.g.D) * sizeof(uint16_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_paths<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_paths<T, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_paths<T><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
+    k_paths<T, GT><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
     return cudaGetLastError();
+}
+
+// The common lane counts (windows of 2r + 1 for r = 2 and 4; full range) are
+// compile-time constants in their own instantiations: index arithmetic on
+// G folds away, which shortens every step.
+template <typename T>
+cudaError_t launch_t(const Buffers &b, const PathPlan &plan, cudaStream_t st)
+{
+    switch (plan.lanes) {
+    case 2: return launch_g<T, 2>(b, plan, st);
+    case 3: return launch_g<T, 3>(b, plan, st);
+    case 32: return launch_g<T, 32>(b, plan, st);
+    default: return launch_g<T, 0>(b, plan, st);
+    }
 }
 
 }  // namespace

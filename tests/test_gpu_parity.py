@@ -49,7 +49,7 @@ def test_tiny_pair_full_then_reduced(rs, orc):
 @pytest.mark.parametrize("overrides", [
     dict(path_mask=0x0F), dict(path_mask=0xF0), dict(path_mask=0x10), dict(path_mask=0x02),
     dict(census_w=7, census_h=7), dict(census_w=9, census_h=7), dict(census_w=3, census_h=3),
-    dict(radius_mode=1), dict(radius_mode=2), dict(radius=0), dict(radius=16),
+    dict(radius_mode=1), dict(radius_mode=2), dict(radius_mode=2, max_disp=128), dict(radius=0), dict(radius=16),
     dict(P1=30, P2=12), dict(P1=0, P2=0), dict(tau_disc=0.5, p_reset=40.0), dict(gate_gamma=0.5, q=0.0),
 ])
 def test_tiny_pair_parameter_variants(rs, orc, overrides):
