@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=32, help="camera streams per GPU")
     ap.add_argument("--radius", type=int, default=4)
+    ap.add_argument("--handles", type=int, default=2,
+                    help="the GPU's streams are split over this many handles on as many CUDA streams")
     ap.add_argument("--mixed", action="store_true",
                     help="also time the mixed-resolution group (6x640x480/D64, 6x1242x375/D128, 4x1920x1080/D256)")
     ap.add_argument("--serve", action="store_true",
@@ -340,24 +342,62 @@ def run_ours(args, rank, world, local_rank):
                 rs.rsgm_reduced_frame(h, host[0][k], host[1][k], Rm[k], tv[k], K, BASE)
                 rs.rsgm_state(h, out[0], None, out[1], None)
 
-    with torch.cuda.stream(stream), ClockSampler(local_rank) as clk:
+    # The streams are split over `handles` handles, each on a CUDA stream of
+    # its own: their kernels overlap, filling the tails of each other's launches.
+    nh = max(1, min(args.handles, B))
+    cut = [B * i // nh for i in range(nh + 1)]
+    parts = []
+    for i in range(nh):
+        a, z = cut[i], cut[i + 1]
+        Ph = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=z - a)
+        cs = torch.cuda.Stream(dev)
+        parts.append((rs.Stream(Ph, cs), cs, a, z))
+
+    def run_parts(frames, host=None, out=None):
+        for k in frames:
+            for ph, cs, a, z in parts:
+                with torch.cuda.stream(cs):
+                    if host is None:
+                        rs.rsgm_reduced_frame(ph.handle, left[k][a:z], right[k][a:z], Rm[k][a:z], tv[k][a:z], K, BASE)
+                    else:
+                        rs.rsgm_reduced_frame(ph.handle, host[0][k][a:z], host[1][k][a:z], Rm[k][a:z], tv[k][a:z],
+                                              K, BASE)
+                        rs.rsgm_state(ph.handle, out[0][a:z], None, out[1][a:z], None)
+
+    def start_parts(host=None):
+        src = host if host is not None else (left, right)
+        for ph, cs, a, z in parts:
+            with torch.cuda.stream(cs):
+                ph.full_frame(src[0][0][a:z], src[1][0][a:z])
+
+    def timed_parts(frames, host=None, out=None):
+        main = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for _, cs, _, _ in parts:
+            cs.wait_event(e0)
+        run_parts(frames, host, out)
+        for _, cs, _, _ in parts:
+            ev = torch.cuda.Event()
+            ev.record(cs)
+            main.wait_event(ev)
+        e1.record(main)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    with ClockSampler(local_rank) as clk:
         # the sampler runs from the warm-up on, so that it sees the GPU under load
-        gs.full_frame(left[0], right[0])
-        run(gs.handle, range(1, 2))
-        tuned = rs.rsgm_autotune(gs.handle)   # aggregation schedule for this workload
-        run(gs.handle, range(2, 1 + args.warmup))
-        gs.sync()
-        f0, c0, _ = gs.counters()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start_parts()
+        run_parts(range(1, 2))
+        tuned = [rs.rsgm_autotune(ph.handle) for ph, _, _, _ in parts]   # aggregation schedule per handle
+        run_parts(range(2, 1 + args.warmup))
+        torch.cuda.synchronize()
+        c0 = sum(ph.counters()[1] for ph, _, _, _ in parts)
         barrier()
         torch.cuda.synchronize()
-        ev0.record(stream)
-        run(gs.handle, range(1 + args.warmup, nframes))
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        elapsed = max_over_ranks(timed_parts(range(1 + args.warmup, nframes)))
         barrier()
-        f1, c1, _ = gs.counters()
+        c1 = sum(ph.counters()[1] for ph, _, _, _ in parts)
     steps = args.steps
     frames_all = B * steps * world
     cells_local = c1 - c0
@@ -374,7 +414,9 @@ def run_ours(args, rank, world, local_rank):
               "cell_updates_per_s": cells_all * N_PATHS / elapsed,
               "cells_per_frame": cells_local / (B * steps),
               "lines_per_warp_tuned": tuned,
-              "gpu_launches": 8 * steps,
+              "handles": "%d handles of %s streams on %d CUDA streams" % (
+                  nh, "/".join(str(cut[i + 1] - cut[i]) for i in range(nh)), nh),
+              "gpu_launches": 8 * steps * nh,
               "clocks": clk.summary()}
 
     # ---- dominant kernel: stage times with CUDA events on the launching stream
@@ -406,22 +448,18 @@ def run_ours(args, rank, world, local_rank):
                           "share_of_step": agg_ms / total_ms if total_ms else None}
 
     if not args.no_extras:
-        # ---- e2e through the C ABI with host buffers (pinned), copies in the timed region
+        # ---- e2e through the C ABI with host buffers (pinned), copies in the
+        # timed region, on the same handles: one handle's copies overlap the
+        # other handles' kernels.
         hl = left.cpu().pin_memory()
         hr = right.cpu().pin_memory()
         outd = torch.empty(B, H, W, dtype=torch.float32).pin_memory()
         outm = torch.empty(B, H, W, dtype=torch.uint8).pin_memory()
-        with torch.cuda.stream(stream):
-            gs.full_frame(hl[0], hr[0])
-            run(gs.handle, range(1, 1 + args.warmup), host=(hl, hr), out=(outd, outm))
-            gs.sync()
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            run(gs.handle, range(1 + args.warmup, nframes), host=(hl, hr), out=(outd, outm))
-            e1.record(stream)
-            torch.cuda.synchronize()
-        e2e_el = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        start_parts(host=(hl, hr))
+        run_parts(range(1, 1 + args.warmup), host=(hl, hr), out=(outd, outm))
+        torch.cuda.synchronize()
+        barrier()
+        e2e_el = max_over_ranks(timed_parts(range(1 + args.warmup, nframes), host=(hl, hr), out=(outd, outm)))
         result["e2e"] = {"value": frames_all / e2e_el, "unit": "frames/s",
                          "h2d_bytes_per_step": 2 * B * H * W, "d2h_bytes_per_step": B * H * W * 5}
 
@@ -498,6 +536,8 @@ def run_ours(args, rank, world, local_rank):
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)
     gs.close()
+    for ph, _, _, _ in parts:
+        ph.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
 
