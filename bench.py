@@ -35,11 +35,12 @@ METRIC = "frames/s and cost-cell updates/s at 1242x375 vs plain form; p99 latenc
 # running minimum for the next pixel, + into S.
 OPS_PER_CELL_PATH = 9
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of the
-# dominant kernel, from the ncu capture in profiles/k_paths_kitti_b8.md
-# (8 streams: 665.2 MB for 51.7 M cells); the 32-stream launch is too large
-# to capture, and its traffic is this figure times its cells.  None once the
-# kernel changes without a new capture.
-NCU_DRAM_BYTES_PER_CELL = 12.86
+# dominant kernel, from the ncu capture in profiles/k_paths_kitti_b32.md: one
+# 32-stream launch, 4.021 GB for 202.0 M cells (the cells of that step are
+# the mean over the run's timed steps).  The traffic reported is this figure
+# times the launch's cells.  None once the kernel changes without a new
+# capture.
+NCU_DRAM_BYTES_PER_CELL = 19.91
 
 
 def parse():
@@ -50,6 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=32, help="camera streams per GPU")
     ap.add_argument("--radius", type=int, default=4)
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="aggregation lines per warp for every handle (0: autotune each handle)")
     ap.add_argument("--handles", type=int, default=2,
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
     ap.add_argument("--mixed", action="store_true",
@@ -353,6 +356,12 @@ def run_ours(args, rank, world, local_rank):
         cs = torch.cuda.Stream(dev)
         parts.append((rs.Stream(Ph, cs), cs, a, z))
 
+    def tune(h):
+        if args.schedule > 0:
+            rs.rsgm_set_schedule(h, args.schedule)
+            return args.schedule
+        return rs.rsgm_autotune(h)
+
     def run_parts(frames, host=None, out=None):
         for k in frames:
             for ph, cs, a, z in parts:
@@ -389,7 +398,7 @@ def run_ours(args, rank, world, local_rank):
         # the sampler runs from the warm-up on, so that it sees the GPU under load
         start_parts()
         run_parts(range(1, 2))
-        tuned = [rs.rsgm_autotune(ph.handle) for ph, _, _, _ in parts]   # aggregation schedule per handle
+        tuned = [tune(ph.handle) for ph, _, _, _ in parts]   # aggregation schedule per handle
         run_parts(range(2, 1 + args.warmup))
         torch.cuda.synchronize()
         c0 = sum(ph.counters()[1] for ph, _, _, _ in parts)
@@ -421,11 +430,13 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- dominant kernel: stage times with CUDA events on the launching stream
     with torch.cuda.stream(stream):
-        rs.rsgm_enable_stage_timing(gs.handle, True)
         gs.full_frame(left[0], right[0])
+        run(gs.handle, range(1, 2))
+        tune(gs.handle)
+        rs.rsgm_enable_stage_timing(gs.handle, True)
         rs.rsgm_stage_times(gs.handle)
         c_before = gs.counters()[1]
-        run(gs.handle, range(1, nframes))
+        run(gs.handle, range(2, nframes))
         st_ms, st_frames = rs.rsgm_stage_times(gs.handle)
         c_after = gs.counters()[1]
         rs.rsgm_enable_stage_timing(gs.handle, False)
@@ -442,7 +453,7 @@ def run_ours(args, rank, world, local_rank):
                           "peak": int_peak_tops, "unit": "Tops/s", "frac": achieved_tops / int_peak_tops,
                           "traffic": (NCU_DRAM_BYTES_PER_CELL * cells_per_frame
                                       if NCU_DRAM_BYTES_PER_CELL else None),
-                          "traffic_unit": "bytes per launch (ncu, scaled by cells from 8 streams)",
+                          "traffic_unit": "bytes per launch (ncu per-cell figure of a 32-stream launch x this launch's cells)",
                           "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_max,
                           "ops_per_cell_path": OPS_PER_CELL_PATH,
                           "share_of_step": agg_ms / total_ms if total_ms else None}
