@@ -74,9 +74,12 @@ def lib():
             L.orc_predict_variance.restype = f32
             L.orc_warp.argtypes = [P, P, i32, i32, P, P, P, f32, f32, P, P, P, P, P]
             L.orc_resolve.argtypes = [P, P, P, i32, i32, i32, i32, i32, f32, f32, P, P, P, P, P]
+            L.orc_resolve_map.argtypes = [P, P, P, i32, i32, i32, i32, i32, P, f32, f32, P, P, P, P, P]
             L.orc_kalman_update32.argtypes = [f32, f32, i32, f32, f32, f32, P, P, P, P]
             L.orc_kalman32.argtypes = [P, P, P, P, i64, f32, f32, P, P, P, P]
             L.orc_kalman64.argtypes = [P, P, P, P, i64, f32, f32, P, P]
+            L.orc_kalman32_rmap.argtypes = [P, P, P, P, i64, P, f32, P, P, P, P]
+            L.orc_kalman64_rmap.argtypes = [P, P, P, P, i64, P, f32, P, P]
             L.orc_median3.argtypes = [P, i32, i32, P]
             L.orc_abs_innovation_q.argtypes = [P, P, i64, P]
             L.orc_integral.argtypes = [P, i32, i32, P]
@@ -109,7 +112,7 @@ class Params:
     census_w: int = 5
     census_h: int = 5
     path_mask: int = 0xFF
-    radius_mode: int = 0          # 0 fixed +-radius, 1 +-ceil(p), 2 full range (plain form)
+    radius_mode: int = 0          # 0 fixed +-radius, 1 +-ceil(p), 2 full range (plain form), 3 per-pixel map
     radius: int = 4
     P1: int = 6
     P2: int = 65
@@ -216,16 +219,21 @@ def warp(d, p, Rm, t, K, b, q, per_source=False):
     return d0, p0, known0
 
 
-def resolve(d0, p0, known0, D, radius_mode, radius, p_reset, tau_disc):
+def resolve(d0, p0, known0, D, radius_mode, radius, p_reset, tau_disc, radius_map=None):
+    """Hole fill, reset and windows; radius_mode 3 takes the half-width of
+    each predicted pixel from radius_map (uint8 H x W)."""
     H, W = d0.shape
     d_pred = np.zeros((H, W), np.float32)
     p_pred = np.zeros((H, W), np.float32)
     cls = np.zeros((H, W), np.uint8)
     lo = np.zeros((H, W), np.uint16)
     wd = np.zeros((H, W), np.uint16)
-    lib().orc_resolve(_p(np.ascontiguousarray(d0, np.float32)), _p(np.ascontiguousarray(p0, np.float32)),
-                      _p(np.ascontiguousarray(known0, np.uint8)), W, H, D, radius_mode, radius,
-                      float(p_reset), float(tau_disc), _p(d_pred), _p(p_pred), _p(cls), _p(lo), _p(wd))
+    rmap = None if radius_map is None else np.ascontiguousarray(radius_map, np.uint8)
+    if radius_mode == 3 and rmap is None:
+        raise ValueError("radius_mode 3 needs a radius map")
+    lib().orc_resolve_map(_p(np.ascontiguousarray(d0, np.float32)), _p(np.ascontiguousarray(p0, np.float32)),
+                          _p(np.ascontiguousarray(known0, np.uint8)), W, H, D, radius_mode, radius, _p(rmap),
+                          float(p_reset), float(tau_disc), _p(d_pred), _p(p_pred), _p(cls), _p(lo), _p(wd))
     return d_pred, p_pred, cls, lo, wd
 
 
@@ -242,6 +250,7 @@ def _f32(a):
 
 
 def kalman32(d_pred, p_pred, cls, d_z, r, gamma):
+    """r: a scalar, or a float32 map of per-pixel measurement variances."""
     d_pred, p_pred, d_z = _f32(d_pred), _f32(p_pred), _f32(d_z)
     cls = np.ascontiguousarray(cls, np.uint8)
     shape = d_pred.shape
@@ -250,8 +259,12 @@ def kalman32(d_pred, p_pred, cls, d_z, r, gamma):
     p = np.zeros(shape, np.float32)
     mask = np.zeros(shape, np.uint8)
     nu = np.zeros(shape, np.float32)
-    lib().orc_kalman32(_p(d_pred), _p(p_pred), _p(cls), _p(d_z), n, r, gamma,
-                       _p(d), _p(p), _p(mask), _p(nu))
+    if np.ndim(r) == 0:
+        lib().orc_kalman32(_p(d_pred), _p(p_pred), _p(cls), _p(d_z), n, float(r), gamma,
+                           _p(d), _p(p), _p(mask), _p(nu))
+    else:
+        lib().orc_kalman32_rmap(_p(d_pred), _p(p_pred), _p(cls), _p(d_z), n, _p(_f32(r)), gamma,
+                                _p(d), _p(p), _p(mask), _p(nu))
     return d, p, mask, nu
 
 
@@ -261,20 +274,28 @@ def kalman64(d_pred, p_pred, cls, d_z, r, gamma):
     shape = d_pred.shape
     d = np.zeros(shape, np.float64)
     p = np.zeros(shape, np.float64)
-    lib().orc_kalman64(_p(d_pred), _p(p_pred), _p(cls), _p(d_z), d_pred.size, r, gamma, _p(d), _p(p))
+    if np.ndim(r) == 0:
+        lib().orc_kalman64(_p(d_pred), _p(p_pred), _p(cls), _p(d_z), d_pred.size, float(r), gamma, _p(d), _p(p))
+    else:
+        lib().orc_kalman64_rmap(_p(d_pred), _p(p_pred), _p(cls), _p(d_z), d_pred.size, _p(_f32(r)), gamma,
+                                _p(d), _p(p))
     return d, p
 
 
 # ---------------------------------------------------------------- one frame
 
-def frame(P: Params, left: np.ndarray, right: np.ndarray, state=None, motion=None):
+def frame(P: Params, left: np.ndarray, right: np.ndarray, state=None, motion=None, radius_map=None,
+          r_map=None):
     """One frame of the method for one camera stream.
 
     ``state`` is ``(d, p)`` of the previous frame (float32 H x W) and
     ``motion`` is ``(R, t, K, b)`` (X_k = R X_{k-1} + t).  Without a state the
     frame is the paper's initial one: the whole disparity range is searched and
-    every pixel takes the measurement (Section 2.4, last paragraph).  Returns a
-    dict of every intermediate and the new state.
+    every pixel takes the measurement (Section 2.4, last paragraph).  With
+    ``radius_map`` (uint8 H x W, used when P.radius_mode == 3) and ``r_map``
+    (float32 H x W) the window half-width and the measurement variance are
+    per pixel, as the learned window chooses them.  Returns a dict of every
+    intermediate and the new state.
     """
     H, W, D = P.height, P.width, P.max_disp
     nbits = census_bits(P.census_w, P.census_h)
@@ -291,14 +312,15 @@ def frame(P: Params, left: np.ndarray, right: np.ndarray, state=None, motion=Non
         Rm, t, K, b = motion
         d0, p0, known0 = warp(state[0], state[1], Rm, t, K, b, P.q)
         d_pred, p_pred, cls, lo, wd = resolve(d0, p0, known0, D, P.radius_mode, P.radius,
-                                              P.reset_variance(), P.tau_disc)
+                                              P.reset_variance(), P.tau_disc, radius_map)
         out.update(d0=d0, p0=p0, known0=known0)
     off, n = offsets(wd)
     cv = cost(cl, cr, lo, wd, off, n, nbits)
     S = aggregate(cv, lo, wd, off, n, P.path_mask, P.P1, P.P2)
     d_int, d_z = wta(S, lo, wd, off)
-    d, p, mask, nu = kalman32(d_pred, p_pred, cls, d_z, P.r_meas, P.gate_gamma)
-    d64, p64 = kalman64(d_pred, p_pred, cls, d_z, P.r_meas, P.gate_gamma)
+    r = P.r_meas if r_map is None else _f32(r_map)
+    d, p, mask, nu = kalman32(d_pred, p_pred, cls, d_z, r, P.gate_gamma)
+    d64, p64 = kalman64(d_pred, p_pred, cls, d_z, r, P.gate_gamma)
     out.update(lo=lo, wd=wd, off=off, ncells=n, cls=cls, d_pred=d_pred, p_pred=p_pred,
                cost=cv, S=S, d_int=d_int, d_z=d_z, d=d, p=p, mask=mask, nu=nu,
                d64=d64, p64=p64)

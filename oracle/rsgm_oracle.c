@@ -347,9 +347,26 @@ void orc_warp(const float *d, const float *p, int W, int H, const float *R, cons
  * (mode 1, the paper's d +- p reading); mode 2 keeps the full range for every
  * pixel (the plain form: full-range SGM + Kalman).
  */
+void orc_resolve_map(const float *d0, const float *p0, const uint8_t *known0, int W, int H, int D,
+                     int radius_mode, int radius, const uint8_t *radius_map, float p_reset,
+                     float tau_disc, float *d_pred, float *p_pred, uint8_t *cls, uint16_t *lo,
+                     uint16_t *wd);
+
 void orc_resolve(const float *d0, const float *p0, const uint8_t *known0, int W, int H, int D,
                  int radius_mode, int radius, float p_reset, float tau_disc, float *d_pred,
                  float *p_pred, uint8_t *cls, uint16_t *lo, uint16_t *wd)
+{
+    orc_resolve_map(d0, p0, known0, W, H, D, radius_mode, radius, NULL, p_reset, tau_disc, d_pred,
+                    p_pred, cls, lo, wd);
+}
+
+/* The same with radius_mode 3: the half-width of a predicted pixel is
+ * radius_map[i], one value per pixel (the learned window: a per-pixel radius
+ * chosen before the search; the ragged volume accepts any width). */
+void orc_resolve_map(const float *d0, const float *p0, const uint8_t *known0, int W, int H, int D,
+                     int radius_mode, int radius, const uint8_t *radius_map, float p_reset,
+                     float tau_disc, float *d_pred, float *p_pred, uint8_t *cls, uint16_t *lo,
+                     uint16_t *wd)
 {
     int64_t n = (int64_t)W * H;
     uint8_t *known1 = (uint8_t *)malloc((size_t)n);
@@ -419,6 +436,8 @@ void orc_resolve(const float *d0, const float *p0, const uint8_t *known0, int W,
             if (radius_mode == 1) {
                 float cp = ceilf(p_pred[i]);
                 h = cp < 1.0f ? 1 : (cp > (float)D ? D : (int)cp);
+            } else if (radius_mode == 3) {
+                h = radius_map[i];
             } else {
                 h = radius;
             }
@@ -485,13 +504,37 @@ void orc_kalman32(const float *d_pred, const float *p_pred, const uint8_t *cls, 
                             &mask[i], &nu[i]);
 }
 
+/* The same with a measurement variance per pixel (r_map[i]). */
+void orc_kalman32_rmap(const float *d_pred, const float *p_pred, const uint8_t *cls,
+                       const float *d_z, int64_t n, const float *r_map, float gamma, float *d,
+                       float *p, uint8_t *mask, float *nu)
+{
+    for (int64_t i = 0; i < n; i++)
+        orc_kalman_update32(d_pred[i], p_pred[i], cls[i], d_z[i], r_map[i], gamma, &d[i], &p[i],
+                            &mask[i], &nu[i]);
+}
+
 /* The same correction in double precision from the same single-precision
  * inputs; the gate decision is taken in single precision (as on the device)
  * so that both forms treat the same pixels as moving. */
+void orc_kalman64_rmap(const float *d_pred, const float *p_pred, const uint8_t *cls,
+                       const float *d_z, int64_t n, const float *r_map, float gamma, double *d,
+                       double *p);
+
 void orc_kalman64(const float *d_pred, const float *p_pred, const uint8_t *cls, const float *d_z,
                   int64_t n, float r, float gamma, double *d, double *p)
 {
+    for (int64_t i = 0; i < n; i++)
+        orc_kalman64_rmap(d_pred + i, p_pred + i, cls + i, d_z + i, 1, &r, gamma, d + i, p + i);
+}
+
+/* Per-pixel measurement variance r_map[i]. */
+void orc_kalman64_rmap(const float *d_pred, const float *p_pred, const uint8_t *cls,
+                       const float *d_z, int64_t n, const float *r_map, float gamma, double *d,
+                       double *p)
+{
     for (int64_t i = 0; i < n; i++) {
+        const float r = r_map[i];
         if (cls[i] == 2) {
             d[i] = d_z[i];
             p[i] = r;
