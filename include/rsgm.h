@@ -68,6 +68,8 @@ extern "C" {
 #define RSGM_RADIUS_FIXED 0     /* [c - radius, c + radius], c = round(d_pred) */
 #define RSGM_RADIUS_VARIANCE 1  /* half-width ceil(p_pred) clamped to [1, D]: the paper's d +- p */
 #define RSGM_RADIUS_FULL 2      /* whole range [0, D): plain SGM + Kalman ("plain form") */
+#define RSGM_RADIUS_LEARNED 3   /* half-width and measurement variance per pixel from an attached
+                                   network (rsgm_attach_cnn); r_meas is then unused */
 
 #define RSGM_MAX_BATCH 256
 #define RSGM_MAX_DISP 256
@@ -160,6 +162,11 @@ int rsgm_set_state(rsgm_stream s, const float *disp, const float *var);
 #define RSGM_BUF_AGGREGATED 8 /* uint16 per cell: S, the sum over enabled paths of Eq. 1 */
 #define RSGM_BUF_D_MEAS 9     /* float per pixel: sub-pixel measurement d_z */
 #define RSGM_BUF_INNOVATION 10 /* float per pixel: d_z - d_pred (0 where class 2) */
+/* RSGM_RADIUS_LEARNED handles only (the latest reduced frame): */
+#define RSGM_BUF_CNN_INPUT 11 /* bfloat16 x 16 per pixel: the network's 4 inputs, then 12 zeros */
+#define RSGM_BUF_CNN_OUTPUT 12 /* float x 8 per pixel: 5 class logits, log r, 2 unused */
+#define RSGM_BUF_RADIUS 13    /* uint8 per pixel: the decided half-width */
+#define RSGM_BUF_R_MEAS 14    /* float per pixel: the decided measurement variance */
 
 /* Copies buffer `which` into dst (device or host) if capacity >= its size;
  * *bytes receives the size (may be queried with dst = NULL).  Synchronises
@@ -299,6 +306,70 @@ int rsgm_group_reduced_frame(rsgm_group g, const uint8_t *const *left, const uin
 
 /* Waits for the group's work and frees it (not its members).  NULL is a no-op. */
 int rsgm_group_destroy(rsgm_group g);
+
+/*
+ * The learned search window.  The paper sizes each pixel's search range from
+ * its predicted variance (Section 2.4, d_pred +- p).  This variant lets a
+ * per-pixel network choose the half-width from {1, 2, 4, 8, 16} and the
+ * measurement variance r of the Kalman correction (Eqs. 5-6).  Its inputs
+ * come from the hole-filled prediction before the discontinuity reset:
+ * d / D, sqrt(p) / D, census Hamming distance at the rounded predicted
+ * disparity / census bits, and Sobel magnitude / 2040.  A pixel without a
+ * prediction takes 0, 1 and 1 for the first three.
+ *
+ * The network has 4 layers of 3x3 correlations with zero padding and ReLU
+ * between them: 4 -> 32 -> 32 -> 32 -> 6 channels.  It runs in bfloat16 with
+ * fp32 accumulation.  The output gives 5 class logits and log r.  The
+ * half-width is the most probable class's radius when its softmax
+ * probability is at least 0.9, else 8.  r = exp(log r), clamped to
+ * [1/16, 64].  Discontinuity resets and pixels without a prediction keep
+ * the full range.
+ *
+ * Parameters are RSGM_CNN_PARAMS floats, layer by layer: weights in
+ * (out, in, ky, kx) order, then the bias.
+ */
+#define RSGM_CNN_PARAMS 21414
+typedef struct rsgm_cnn_s *rsgm_cnn;
+
+/* Creates a network on the current device from host parameters, used and
+ * trained on `cuda_stream` (may be NULL).  Every handle it is attached to
+ * must use the same stream. */
+int rsgm_cnn_create(rsgm_cnn *out, const float *params, void *cuda_stream);
+
+/* Copies the current parameters, or the gradient of the latest training
+ * step, into host memory (RSGM_CNN_PARAMS floats).  Synchronises. */
+int rsgm_cnn_params(rsgm_cnn c, float *params);
+int rsgm_cnn_grad(rsgm_cnn c, float *grad);
+
+/* Frees the network.  Detach it first: destroy, or never again run, every
+ * handle it is attached to.  NULL is a no-op. */
+int rsgm_cnn_destroy(rsgm_cnn c);
+
+/* Attaches the network to a handle created with RSGM_RADIUS_LEARNED (same
+ * device and CUDA stream).  Allocates the handle's per-pixel network buffers:
+ * 261 bytes per pixel, plus 160 at the first training step.  Its reduced
+ * frames then run the network after the prediction.  A learned handle
+ * cannot join a group. */
+int rsgm_attach_cnn(rsgm_stream s, rsgm_cnn c);
+
+/*
+ * One training step on the handle's latest reduced frame, against a target
+ * disparity map (device, B*H*W floats).  The step reruns the network on the
+ * frame's stored inputs with the current parameters, so repeated steps on
+ * one frame descend properly.  The target is typically the state
+ * of a full-range (RSGM_RADIUS_FULL) handle on the same frames.
+ *
+ * Trained pixels are those predicted and not reset (class 0).  Label: the
+ * smallest radius covering |round(target) - round(d_pred)|, with centres
+ * clamped to [0, D - 1], else 16.  Loss: cross-entropy plus
+ * 0.1 * 0.5 (e^2 exp(-s) + s), where e = target - d_pred and s = log r,
+ * averaged over all pixels.  Update: one Adam step (0.9, 0.999, 1e-8) with
+ * learning rate lr; lr = 0 computes the gradient only.
+ *
+ * *loss (host, may be NULL) receives the loss before the step, which
+ * synchronises.  The gradient stays readable by rsgm_cnn_grad.
+ */
+int rsgm_cnn_train_step(rsgm_cnn c, rsgm_stream s, const float *d_target, float lr, float *loss);
 
 /* Waits for the handle's enqueued work; reports deferred device errors. */
 int rsgm_sync(rsgm_stream s);

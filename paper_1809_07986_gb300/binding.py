@@ -24,6 +24,8 @@ RSGM_ERR_CHECK_FAILED = -6
 RSGM_RADIUS_FIXED = 0
 RSGM_RADIUS_VARIANCE = 1
 RSGM_RADIUS_FULL = 2
+RSGM_RADIUS_LEARNED = 3
+RSGM_CNN_PARAMS = 21414
 RSGM_MAX_BATCH = 256
 RSGM_MAX_DISP = 256
 
@@ -38,6 +40,10 @@ RSGM_BUF_COST = 7
 RSGM_BUF_AGGREGATED = 8
 RSGM_BUF_D_MEAS = 9
 RSGM_BUF_INNOVATION = 10
+RSGM_BUF_CNN_INPUT = 11
+RSGM_BUF_CNN_OUTPUT = 12
+RSGM_BUF_RADIUS = 13
+RSGM_BUF_R_MEAS = 14
 
 RSGM_STAGE_PREDICT = 0
 RSGM_STAGE_SCAN = 1
@@ -106,6 +112,12 @@ SIGNATURES = {
     "rsgm_group_reduced_frame": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                                 ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     "rsgm_group_destroy": (ctypes.c_int, [_P]),
+    "rsgm_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P]),
+    "rsgm_cnn_params": (ctypes.c_int, [_P, _P]),
+    "rsgm_cnn_grad": (ctypes.c_int, [_P, _P]),
+    "rsgm_cnn_destroy": (ctypes.c_int, [_P]),
+    "rsgm_attach_cnn": (ctypes.c_int, [_P, _P]),
+    "rsgm_cnn_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
     "rsgm_sync": (ctypes.c_int, [_P]),
     "rsgm_destroy_stream": (ctypes.c_int, [_P]),
     "rsgm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -321,6 +333,48 @@ def rsgm_group_reduced_frame(g: int, lefts, rights, Rs, ts, Ks, baselines):
 
 def rsgm_group_destroy(g: int):
     _check(lib().rsgm_group_destroy(g), "rsgm_group_destroy")
+
+
+def rsgm_cnn_create(params, cuda_stream=None) -> int:
+    """params: RSGM_CNN_PARAMS floats (host array or CPU tensor)."""
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    a = _host_f32(params, RSGM_CNN_PARAMS)
+    c = _P()
+    _check(lib().rsgm_cnn_create(ctypes.byref(c), _ptr(a), cuda_stream), "rsgm_cnn_create")
+    return c.value
+
+
+def _cnn_vector(fn, c: int, where: str):
+    import numpy as np
+    out = np.zeros(RSGM_CNN_PARAMS, np.float32)
+    _check(fn(c, _ptr(out)), where)
+    return out
+
+
+def rsgm_cnn_params(c: int):
+    return _cnn_vector(lib().rsgm_cnn_params, c, "rsgm_cnn_params")
+
+
+def rsgm_cnn_grad(c: int):
+    return _cnn_vector(lib().rsgm_cnn_grad, c, "rsgm_cnn_grad")
+
+
+def rsgm_cnn_destroy(c: int):
+    _check(lib().rsgm_cnn_destroy(c), "rsgm_cnn_destroy")
+
+
+def rsgm_attach_cnn(h: int, c: int):
+    _check(lib().rsgm_attach_cnn(h, c), "rsgm_attach_cnn")
+
+
+def rsgm_cnn_train_step(c: int, h: int, d_target, lr: float, want_loss: bool = True):
+    """One training step against d_target (device, B*H*W floats); returns the
+    loss (synchronises) or None."""
+    loss = ctypes.c_float()
+    _check(lib().rsgm_cnn_train_step(c, h, _ptr(d_target), float(lr), ctypes.byref(loss) if want_loss else None),
+           "rsgm_cnn_train_step")
+    return loss.value if want_loss else None
 
 
 def rsgm_sync(h: int):

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
                                                 uint32_t *__restrict__ win, uint8_t *__restrict__ cls,
                                                 uint32_t *__restrict__ inrow,
                                                 uint32_t *__restrict__ row_total,
-                                                unsigned long long *__restrict__ key, Geometry g,
+                                                unsigned long long *__restrict__ key,
+                                                const uint8_t *__restrict__ radius_map, Geometry g,
                                                 FrameParams fp)
 {
     __shared__ float sd[3][kWinTile + 2];  // rows y-1, y, y+1; column x0 - 1 + i at index i
@@ -219,6 +220,8 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
                         if (fp.radius_mode == RSGM_RADIUS_VARIANCE) {
                             float cp = ceilf(p_pred[gi]);
                             h = cp < 1.0f ? 1 : (cp > (float)g.D ? g.D : (int)cp);
+                        } else if (fp.radius_mode == RSGM_RADIUS_LEARNED) {
+                            h = radius_map[gi];
                         } else {
                             h = fp.radius;
                         }
@@ -309,8 +312,9 @@ cudaError_t launch_gather_fill(const Buffers &b, const Geometry &g, float q, cud
 
 cudaError_t launch_window(const Buffers &b, const Geometry &g, const FrameParams &fp, cudaStream_t st)
 {
+    if (fp.radius_mode == RSGM_RADIUS_LEARNED && !b.radius) return cudaErrorInvalidValue;
     k_window<<<(unsigned)(g.B * g.H), 256, 0, st>>>(b.d_pred, b.p_pred, b.win, b.cls, b.inrow,
-                                                     b.row_total, b.key, g, fp);
+                                                     b.row_total, b.key, b.radius, g, fp);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,16 @@ struct rsgm_stream_s {
     float p_reset;
     bool has_state;
     Buffers buf;
+    rsgm_cnn cnn;         // attached network (RSGM_RADIUS_LEARNED), not owned
+    LearnedBuffers lb;    // its per-pixel buffers, owned
+    bool learned_frame;   // the latest frame ran the network
+};
+
+struct rsgm_cnn_s {
+    int device;
+    cudaStream_t st;
+    CnnWeights w;
+    int step;  // Adam steps taken
 };
 
 namespace {
@@ -108,7 +118,7 @@ int check_params(const rsgm_params *p)
         return fail(RSGM_ERR_INVALID_ARG, "census window must be odd, <= 15 and have <= 64 bits");
     if (p->path_mask == 0 || p->path_mask > 0xFFu)
         return fail(RSGM_ERR_INVALID_ARG, "path_mask must enable 1..8 of the 8 directions");
-    if (p->radius_mode < RSGM_RADIUS_FIXED || p->radius_mode > RSGM_RADIUS_FULL)
+    if (p->radius_mode < RSGM_RADIUS_FIXED || p->radius_mode > RSGM_RADIUS_LEARNED)
         return fail(RSGM_ERR_INVALID_ARG, "unknown radius_mode %d", p->radius_mode);
     if (p->radius < 0) return fail(RSGM_ERR_INVALID_ARG, "radius must be >= 0");
     if (p->P1 < 0 || p->P2 < 0 || p->P1 > 4000 || p->P2 > 4000)
@@ -144,6 +154,27 @@ void free_buffers(Buffers &b)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(&b, 0, sizeof(b));
+}
+
+void free_learned(LearnedBuffers &lb)
+{
+    void *ptrs[] = {lb.feats, lb.act[0], lb.act[1], lb.act[2], lb.out, lb.radius, lb.r_map, lb.g16, lb.ga, lb.gb,
+                    lb.loss};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    memset(&lb, 0, sizeof(lb));
+}
+
+void free_cnn(rsgm_cnn c)
+{
+    void *ptrs[] = {c->w.theta, c->w.m, c->w.v, c->w.grad};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int l = 0; l < kCnnLayers; ++l) {
+        if (c->w.wf[l]) cudaFree(c->w.wf[l]);
+        if (c->w.wb[l]) cudaFree(c->w.wb[l]);
+        if (c->w.bias[l]) cudaFree(c->w.bias[l]);
+    }
 }
 
 FrameParams frame_params(const rsgm_stream_s *s)
@@ -197,21 +228,23 @@ int mark(rsgm_stream s, int k)
         if (rc_) return rc_;         \
     } while (0)
 
-// Census, cost, aggregation and the update: the part shared by both frame kinds.
-int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr)
+// Census, cost, aggregation and the update: the part shared by both frame
+// kinds.  A learned frame has run the census already (the network reads it)
+// and corrects with its per-pixel measurement variance r_map.
+int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool census_done, const float *r_map)
 {
     const Geometry &g = s->g;
     FrameParams fp = frame_params(s);
     RSGM_MARK(s, 1);
     RSGM_CUDA(launch_row_scan(s->buf, g, s->st));
     RSGM_MARK(s, 2);
-    RSGM_CUDA(launch_census(s->buf, g, dl, dr, s->P.census_w, s->P.census_h, s->st));
+    if (!census_done) RSGM_CUDA(launch_census(s->buf, g, dl, dr, s->P.census_w, s->P.census_h, s->st));
     RSGM_MARK(s, 3);
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
     RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, s->tuned_lines, s->st));
     RSGM_MARK(s, 5);
-    RSGM_CUDA(launch_update(s->buf, g, fp, s->nplanes, s->plane_bytes, s->st));
+    RSGM_CUDA(launch_update(s->buf, g, fp, r_map, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
     return RSGM_OK;
 }
@@ -225,6 +258,8 @@ int check_reduced_args(rsgm_stream s, const uint8_t *left, const uint8_t *right,
         K[6] != 0.0f || K[7] != 0.0f || K[8] != 1.0f)
         return fail(RSGM_ERR_INVALID_ARG, "K must be [fx 0 cx; 0 fy cy; 0 0 1] with fx, fy > 0; baseline > 0");
     if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "reduced frame before any full frame or set_state");
+    if (s->P.radius_mode == RSGM_RADIUS_LEARNED && !s->cnn)
+        return fail(RSGM_ERR_INVALID_ARG, "RSGM_RADIUS_LEARNED handle without an attached network");
     return RSGM_OK;
 }
 
@@ -259,9 +294,18 @@ int enqueue_reduced(rsgm_stream s, const uint8_t *left, const uint8_t *right, co
     free(a);
     if (e != cudaSuccess) return cuda_fail(e, "splat launch");
     RSGM_CUDA(launch_gather_fill(s->buf, s->g, s->P.q, s->st));
+    const bool learned = s->P.radius_mode == RSGM_RADIUS_LEARNED;
+    if (learned) {
+        // the network reads the census residual at the predicted disparity
+        RSGM_CUDA(launch_census(s->buf, s->g, dl, dr, s->P.census_w, s->P.census_h, s->st));
+        RSGM_CUDA(cnn_forward(s->cnn->w, s->lb, s->buf, s->g, dl, s->nbits, s->st));
+    }
     FrameParams fp = frame_params(s);
     RSGM_CUDA(launch_window(s->buf, s->g, fp, s->st));
-    return match_and_update(s, dl, dr);
+    rc = match_and_update(s, dl, dr, learned, learned ? s->lb.r_map : nullptr);
+    if (rc) return rc;
+    s->learned_frame = learned;
+    return RSGM_OK;
 }
 
 void destroy_timer(StageTimer &t)
@@ -320,7 +364,8 @@ int rsgm_footprint(const rsgm_params *p, uint64_t *bytes)
     const uint64_t stride = (cells + 15) / 16 * 16;
     const uint64_t per_pixel = 2 + 16 + 8 + 8 + 8 + 4 + 1 + 4 + 8 + 2 + 1 + 4 + 4 + 4 + RSGM_MAX_WINDOW_SIZES;
     *bytes = n * per_pixel + cells * (1 + 2) + 128 + stride * __builtin_popcount(p->path_mask) * plane_bytes +
-             (uint64_t)p->batch * p->height * 8 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32;
+             (uint64_t)p->batch * p->height * 8 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32 +
+             (p->radius_mode == RSGM_RADIUS_LEARNED ? n * 261 : 0);
     return RSGM_OK;
 }
 
@@ -353,7 +398,10 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
     s->plane_bytes = s->nbits + p->P2 <= 255 ? 1 : 2;
     // Lanes per line: enough for the common (predicted) window; wider windows
     // loop.  Full-range modes use a whole warp per line.
-    s->lanes = lanes_per_line(p->radius_mode == RSGM_RADIUS_FIXED ? 2 * p->radius + 1 : p->max_disp);
+    // Learned windows: sized for the fallback half-width 8 (wider ones loop).
+    s->lanes = lanes_per_line(p->radius_mode == RSGM_RADIUS_FIXED     ? 2 * p->radius + 1
+                              : p->radius_mode == RSGM_RADIUS_LEARNED ? 17
+                                                                      : p->max_disp);
     s->p_reset = p->p_reset > 0.0f ? p->p_reset : (float)p->max_disp * (float)p->max_disp / 12.0f;
     s->has_state = false;
     memset(&s->buf, 0, sizeof(s->buf));
@@ -404,9 +452,10 @@ int rsgm_full_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right)
     if (rc) return rc;
     RSGM_MARK(s, 0);
     RSGM_CUDA(launch_full_window(s->buf, s->g, s->st));
-    rc = match_and_update(s, dl, dr);
+    rc = match_and_update(s, dl, dr, false, nullptr);
     if (rc) return rc;
     s->has_state = true;
+    s->learned_frame = false;
     return RSGM_OK;
 }
 
@@ -485,9 +534,14 @@ int rsgm_read_buffer(rsgm_stream s, int which, void *dst, size_t capacity, size_
         case RSGM_BUF_P_PRED: src = s->buf.p_pred; size = n * 4; break;
         case RSGM_BUF_D_MEAS: src = s->buf.d_z; size = n * 4; break;
         case RSGM_BUF_INNOVATION: src = s->buf.nu; size = n * 4; break;
+        case RSGM_BUF_CNN_INPUT: src = s->lb.feats; size = n * 32; break;
+        case RSGM_BUF_CNN_OUTPUT: src = s->lb.out; size = n * kCnnOutPad * 4; break;
+        case RSGM_BUF_RADIUS: src = s->lb.radius; size = n; break;
+        case RSGM_BUF_R_MEAS: src = s->lb.r_map; size = n * 4; break;
         default: return fail(RSGM_ERR_INVALID_ARG, "unknown buffer %d", which);
         }
     }
+    if (size && !src) return fail(RSGM_ERR_INVALID_ARG, "buffer %d does not exist: no network attached", which);
     if (bytes) *bytes = size;
     if (!dst) return RSGM_OK;
     if (capacity < size) return fail(RSGM_ERR_INVALID_ARG, "capacity %zu < %zu bytes", capacity, size);
@@ -648,6 +702,7 @@ int rsgm_destroy_stream(rsgm_stream s)
         cudaError_t e = cudaStreamSynchronize(s->st);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
         free_buffers(s->buf);
+        free_learned(s->lb);
         destroy_timer(s->timer);
     }
     delete s;
@@ -671,6 +726,157 @@ const char *rsgm_status_string(int code)
 const char *rsgm_last_error(void) { return g_last_error; }
 
 // ------------------------------------------------------------------ groups
+
+// ------------------------------------------------------------------ the learned window
+
+int rsgm_cnn_create(rsgm_cnn *out, const float *params, void *cuda_stream)
+{
+    if (!out || !params) return fail(RSGM_ERR_INVALID_ARG, "NULL output or parameters");
+    *out = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    rsgm_cnn c = new (std::nothrow) rsgm_cnn_s();
+    if (!c) return fail(RSGM_ERR_OOM, "host allocation failed");
+    c->device = dev;
+    c->st = (cudaStream_t)cuda_stream;
+    CnnWeights &w = c->w;
+    void *all[40];
+    int nall = 0, rc = RSGM_OK;
+    if ((rc = alloc(&w.theta, kCnnParams, all, nall)) || (rc = alloc(&w.m, kCnnParams, all, nall)) ||
+        (rc = alloc(&w.v, kCnnParams, all, nall)) || (rc = alloc(&w.grad, kCnnParams, all, nall))) {
+        free_cnn(c);
+        delete c;
+        return rc;
+    }
+    for (int l = 0; l < kCnnLayers && rc == RSGM_OK; ++l) {
+        const size_t cinp = l == 0 ? 16 : 32, coutp = l == kCnnLayers - 1 ? kCnnOutPad : 32;
+        const size_t kp = l == kCnnLayers - 1 ? 16 : 32;
+        uint16_t *wf = nullptr, *wb = nullptr;
+        rc = alloc(&wf, 9 * coutp * cinp, all, nall);
+        w.wf[l] = wf;
+        if (!rc && l > 0) {
+            rc = alloc(&wb, 9 * 32 * kp, all, nall);
+            w.wb[l] = wb;
+        }
+        if (!rc) rc = alloc(&w.bias[l], coutp, all, nall);
+    }
+    if (!rc) {
+        if ((e = cudaMemcpyAsync(w.theta, params, kCnnParams * sizeof(float), cudaMemcpyDefault, c->st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w.m, 0, kCnnParams * sizeof(float), c->st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w.v, 0, kCnnParams * sizeof(float), c->st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w.grad, 0, kCnnParams * sizeof(float), c->st)) != cudaSuccess ||
+            (e = cnn_pack(w, c->st)) != cudaSuccess || (e = cudaStreamSynchronize(c->st)) != cudaSuccess)
+            rc = cuda_fail(e, "network initialisation");
+    }
+    if (rc) {
+        free_cnn(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return RSGM_OK;
+}
+
+namespace {
+int cnn_copy_out(rsgm_cnn c, float *host, const float *src)
+{
+    if (!c || !host) return fail(RSGM_ERR_INVALID_ARG, "NULL network or destination");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the network's device");
+    RSGM_CUDA(cudaMemcpyAsync(host, src, kCnnParams * sizeof(float), cudaMemcpyDefault, c->st));
+    RSGM_CUDA(cudaStreamSynchronize(c->st));
+    return RSGM_OK;
+}
+}  // namespace
+
+int rsgm_cnn_params(rsgm_cnn c, float *params) { return cnn_copy_out(c, params, c ? c->w.theta : nullptr); }
+
+int rsgm_cnn_grad(rsgm_cnn c, float *grad) { return cnn_copy_out(c, grad, c ? c->w.grad : nullptr); }
+
+int rsgm_cnn_destroy(rsgm_cnn c)
+{
+    if (!c) return RSGM_OK;
+    int rc = RSGM_OK;
+    {
+        DeviceGuard dg(c->device);
+        cudaError_t e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+        free_cnn(c);
+    }
+    delete c;
+    return rc;
+}
+
+int rsgm_attach_cnn(rsgm_stream s, rsgm_cnn c)
+{
+    if (!s || !c) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or network");
+    if (s->P.radius_mode != RSGM_RADIUS_LEARNED)
+        return fail(RSGM_ERR_INVALID_ARG, "the handle was not created with RSGM_RADIUS_LEARNED");
+    if (s->device != c->device || s->st != c->st)
+        return fail(RSGM_ERR_INVALID_ARG, "the network and the handle must share one device and one CUDA stream");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    if (!s->lb.feats) {
+        LearnedBuffers &lb = s->lb;
+        const size_t n = (size_t)s->g.NPIX;
+        void *all[16];
+        int nall = 0, rc;
+        uint8_t *feats = nullptr, *a0 = nullptr, *a1 = nullptr, *a2 = nullptr;
+        if ((rc = alloc(&feats, n * 32, all, nall)) || (rc = alloc(&a0, n * 64, all, nall)) ||
+            (rc = alloc(&a1, n * 64, all, nall)) || (rc = alloc(&a2, n * 64, all, nall)) ||
+            (rc = alloc(&lb.out, n * kCnnOutPad, all, nall)) || (rc = alloc(&lb.radius, n, all, nall)) ||
+            (rc = alloc(&lb.r_map, n, all, nall))) {
+            for (int i = 0; i < nall; ++i) cudaFree(all[i]);
+            memset(&lb, 0, sizeof(lb));
+            return rc;
+        }
+        lb.feats = feats;
+        lb.act[0] = a0;
+        lb.act[1] = a1;
+        lb.act[2] = a2;
+    }
+    s->cnn = c;
+    s->buf.radius = s->lb.radius;
+    return RSGM_OK;
+}
+
+int rsgm_cnn_train_step(rsgm_cnn c, rsgm_stream s, const float *d_target, float lr, float *loss)
+{
+    if (!c || !s || !d_target) return fail(RSGM_ERR_INVALID_ARG, "NULL network, handle or target");
+    if (s->cnn != c) return fail(RSGM_ERR_INVALID_ARG, "the network is not attached to this handle");
+    if (!s->learned_frame) return fail(RSGM_ERR_NO_STATE, "no learned reduced frame to train on");
+    if (!(lr >= 0.0f)) return fail(RSGM_ERR_INVALID_ARG, "lr must be >= 0");
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    if (!is_device_pointer(d_target)) return fail(RSGM_ERR_INVALID_ARG, "d_target must be device memory");
+    LearnedBuffers &lb = s->lb;
+    if (!lb.g16) {
+        const size_t n = (size_t)s->g.NPIX;
+        void *all[8];
+        int nall = 0, rc;
+        uint8_t *g16 = nullptr, *ga = nullptr, *gb = nullptr;
+        if ((rc = alloc(&g16, n * 32, all, nall)) || (rc = alloc(&ga, n * 64, all, nall)) ||
+            (rc = alloc(&gb, n * 64, all, nall)) || (rc = alloc(&lb.loss, 1, all, nall))) {
+            for (int i = 0; i < nall; ++i) cudaFree(all[i]);
+            lb.loss = nullptr;
+            return rc;
+        }
+        lb.g16 = g16;
+        lb.ga = ga;
+        lb.gb = gb;
+    }
+    RSGM_CUDA(cnn_backward(c->w, lb, s->buf, s->g, d_target, s->sm_count, s->st));
+    if (lr > 0.0f) {
+        c->step++;
+        RSGM_CUDA(cnn_adam(c->w, c->step, lr, s->st));
+    }
+    if (loss) {
+        RSGM_CUDA(cudaMemcpyAsync(loss, lb.loss, sizeof(float), cudaMemcpyDeviceToHost, s->st));
+        RSGM_CUDA(cudaStreamSynchronize(s->st));
+    }
+    return RSGM_OK;
+}
 
 int rsgm_set_schedule(rsgm_stream s, int32_t lines_per_warp)
 {
@@ -768,6 +974,8 @@ int rsgm_group_create(rsgm_group *out, rsgm_stream *members, int32_t n)
     if (!members || n < 1 || n > 64) return fail(RSGM_ERR_INVALID_ARG, "a group has 1 to 64 members");
     for (int k = 0; k < n; ++k) {
         if (!members[k]) return fail(RSGM_ERR_INVALID_ARG, "NULL member");
+        if (members[k]->P.radius_mode == RSGM_RADIUS_LEARNED)
+            return fail(RSGM_ERR_INVALID_ARG, "a learned-window handle cannot join a group");
         if (members[k]->device != members[0]->device || members[k]->st != members[0]->st)
             return fail(RSGM_ERR_INVALID_ARG, "group members must share one device and one CUDA stream");
         for (int j = 0; j < k; ++j)

@@ -87,7 +87,55 @@ struct Buffers {
     float *median;                      // 3x3 median of d, NPIX
     unsigned long long *sat;            // integral image of |nu|, B * (H+1) * (W+1)
     uint8_t *flags;                     // detection flag per window, B * RSGM_MAX_WINDOW_SIZES * H * W
+    const uint8_t *radius;              // learned window half-width per pixel (RSGM_RADIUS_LEARNED), else NULL
 };
+
+// ---- the learned window (RSGM_RADIUS_LEARNED) ----
+
+constexpr int kCnnLayers = 4;
+constexpr int kCnnClasses = 5;   // radius classes 1, 2, 4, 8, 16
+constexpr int kCnnOutPad = 8;    // output channels per pixel: 5 logits, log r, 2 unused
+constexpr int kCnnParams = RSGM_CNN_PARAMS;
+extern const int kCnnIn[kCnnLayers];   // 4, 32, 32, 32
+extern const int kCnnOut[kCnnLayers];  // 32, 32, 32, 6
+
+// Parameters on the device: fp32 master copy (layer by layer, weights
+// (out, in, 3, 3) then bias), Adam moments and the gradient; per layer the
+// bfloat16 forward weights [9][out padded][in padded], the bfloat16
+// input-gradient weights [9][in][gradient channels] (layers 1-3) and the
+// bias padded to the output channels.
+struct CnnWeights {
+    float *theta, *m, *v, *grad;
+    void *wf[kCnnLayers], *wb[kCnnLayers];
+    float *bias[kCnnLayers];
+};
+
+// Per-pixel buffers of a handle running the learned window (bfloat16
+// activations, channels innermost): inputs (16 channels), three hidden
+// layers (32), the output (fp32, kCnnOutPad), the decided half-width and
+// measurement variance; the training gradients (allocated at the first
+// training step) and the loss accumulator.
+struct LearnedBuffers {
+    void *feats;
+    void *act[3];
+    float *out;
+    uint8_t *radius;
+    float *r_map;
+    void *g16, *ga, *gb;
+    float *loss;
+};
+
+long long cnn_param_offset(int layer);
+cudaError_t cnn_pack(const CnnWeights &w, cudaStream_t st);
+// Inputs, the four layers and the decision of the latest prediction.
+cudaError_t cnn_forward(const CnnWeights &w, const LearnedBuffers &lb, const Buffers &b, const Geometry &g,
+                        const uint8_t *left, int nbits, cudaStream_t st);
+// The four layers again from the stored inputs, the loss against d_target
+// and the gradient of every parameter (into w.grad).
+cudaError_t cnn_backward(const CnnWeights &w, const LearnedBuffers &lb, const Buffers &b, const Geometry &g,
+                         const float *d_target, int sm_count, cudaStream_t st);
+// One Adam step (step counted from 1) and the repacked device weights.
+cudaError_t cnn_adam(const CnnWeights &w, int step, float lr, cudaStream_t st);
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
 
@@ -113,7 +161,7 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
 
 // Sum of the planes, winner-takes-all, Kalman correction and gate
 // (Sections 2.2-2.4).
-cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, int nplanes,
+cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, const float *r_map, int nplanes,
                           int plane_bytes, cudaStream_t st);
 
 // After the path (Section 2.3 median output, Section 4 boxes).

@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
                                                         float *__restrict__ d, float *__restrict__ p,
                                                         int16_t *__restrict__ d_int, uint8_t *__restrict__ mask,
                                                         float *__restrict__ d_z, float *__restrict__ nu_out,
-                                                        Geometry g, FrameParams fp)
+                                                        const float *__restrict__ r_map, Geometry g,
+                                                        FrameParams fp)
 {
     extern __shared__ uint16_t sS[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     }
     d_int[gi] = (int16_t)di;
     d_z[gi] = dz;
-    float r = fp.r_meas;
+    float r = r_map ? r_map[gi] : fp.r_meas;  // per pixel with the learned window
     if (cls[gi] == 2) {
         d[gi] = dz;
         p[gi] = r;
@@ -186,8 +187,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
 
 }  // namespace
 
-cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, int nplanes,
-                          int plane_bytes, cudaStream_t st)
+cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, const float *r_map,
+                          int nplanes, int plane_bytes, cudaStream_t st)
 {
     const unsigned blocks = (unsigned)((g.NPIX + kUpdWarps * 32 - 1) / (kUpdWarps * 32));
     const long long stride = plane_stride(g);
@@ -195,11 +196,11 @@ cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams
     if (plane_bytes == 1)
         k_update<uint8_t><<<blocks, kUpdWarps * 32, smem, st>>>((const uint8_t *)b.planes, stride, nplanes, b.S, b.meta,
                                                   b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
-                                                  b.d_z, b.nu, g, fp);
+                                                  b.d_z, b.nu, r_map, g, fp);
     else
         k_update<uint16_t><<<blocks, kUpdWarps * 32, smem, st>>>((const uint16_t *)b.planes, stride, nplanes, b.S, b.meta,
                                                    b.cls, b.d_pred, b.p_pred, b.d, b.p, b.d_int, b.mask,
-                                                   b.d_z, b.nu, g, fp);
+                                                   b.d_z, b.nu, r_map, g, fp);
     return cudaGetLastError();
 }
 

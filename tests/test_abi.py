@@ -58,7 +58,7 @@ def test_defaults_follow_table_1(rs):
 
 @pytest.mark.parametrize("field,value", [
     ("width", 0), ("height", -3), ("max_disp", 0), ("max_disp", 257), ("batch", 0), ("batch", 257),
-    ("census_w", 4), ("census_h", 17), ("path_mask", 0), ("path_mask", 0x100), ("radius_mode", 3),
+    ("census_w", 4), ("census_h", 17), ("path_mask", 0), ("path_mask", 0x100), ("radius_mode", 4),
     ("radius", -1), ("P1", -1), ("P2", 5000), ("r_meas", 0.0), ("q", -1.0), ("gate_gamma", 0.0),
 ])
 def test_bad_parameters_are_rejected_before_device_work(rs, field, value):
@@ -106,3 +106,19 @@ def test_no_gpu_gives_a_cuda_status_not_a_crash(rs):
     with pytest.raises(rs.RsgmError) as e:
         rs.rsgm_init_stream(p)
     assert e.value.code == rs.RSGM_ERR_CUDA
+
+
+def test_cnn_parameter_count_matches_the_oracle_layout(rs):
+    from oracle import learned
+    assert rs.RSGM_CNN_PARAMS == learned.n_params()
+
+
+def test_cnn_entry_points_reject_null_before_device_work(rs):
+    L = rs.lib()
+    c = ctypes.c_void_p()
+    assert L.rsgm_cnn_create(ctypes.byref(c), None, None) == rs.RSGM_ERR_INVALID_ARG
+    assert L.rsgm_cnn_create(None, None, None) == rs.RSGM_ERR_INVALID_ARG
+    assert L.rsgm_attach_cnn(None, None) == rs.RSGM_ERR_INVALID_ARG
+    assert L.rsgm_cnn_train_step(None, None, None, 0.0, None) == rs.RSGM_ERR_INVALID_ARG
+    assert L.rsgm_cnn_params(None, None) == rs.RSGM_ERR_INVALID_ARG
+    assert L.rsgm_cnn_destroy(None) == rs.RSGM_OK
