@@ -57,6 +57,9 @@ def parse():
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
     ap.add_argument("--mixed", action="store_true",
                     help="also time the mixed-resolution group (6x640x480/D64, 6x1242x375/D128, 4x1920x1080/D256)")
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the learned search window on 2000 frames of seeded 384x128 pairs and compare "
+                         "it with the fixed half-width 8 on held-out pairs")
     ap.add_argument("--serve", action="store_true",
                     help="also run the request loop: 32 Poisson streams (10-30 Hz) of 640x480/1242x375/1920x1080")
     ap.add_argument("--no-extras", action="store_true",
@@ -543,6 +546,10 @@ def run_ours(args, rank, world, local_rank):
             result["mixed_group"] = mixed_group(args, dev, stream)
         if args.serve and rank == 0:
             result["serving"] = serving_loop(dev)
+        if args.learned and rank == 0:
+            from paper_1809_07986_gb300 import learned
+            with torch.cuda.device(dev):
+                result["learned_window"] = learned.run()
 
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)
