@@ -12,9 +12,10 @@
 //
 // Activations are bfloat16, pixel-major with the channels innermost
 // (NHWC); the convolutions are implicit GEMMs on the tensor cores
-// (mma.sync m16n8k16, bfloat16 in, fp32 accumulate): a warp computes 16
-// consecutive pixels of one row against all output channels, the K
-// dimension running over the 9 taps x 16-channel chunks.  The input gradient
+// (mma.sync m16n8k16, bfloat16 in, fp32 accumulate) over tiles staged in
+// shared memory: a warp computes 16 consecutive pixels of one row against
+// all output channels, the K dimension running over the 9 taps x 16-channel
+// chunks.  The input gradient
 // of a layer is the same correlation with the weights flipped and
 // transposed, so the forward kernel serves it with a masked epilogue (the
 // ReLU derivative).  Weight gradients are fp32 sums on the CUDA cores.
@@ -92,64 +93,88 @@ __global__ void __launch_bounds__(256) k_features(const uint8_t *__restrict__ le
 
 // One 3x3 layer as an implicit GEMM.  `in` has CINP channels per pixel, `wt`
 // is [9 taps][COUTP][CINP] (B operand: n = output channel, k = input
-// channel).  A warp owns 16 consecutive pixels of one row; lane (group g,
-// thread t) loads the A fragment rows g and g + 8 (pixels) at channels 2t,
-// 2t + 1 and 2t + 8, 2t + 9 of each 16-channel chunk, and the B fragment
-// columns g (output channels) at the same channel offsets; pixels outside
-// the image read zero.  Epilogue by mode: bias + ReLU to bfloat16, bias to
-// fp32, or zeroed where mask <= 0 (the ReLU derivative) to bfloat16.
+// channel).  A block owns kConvPix consecutive pixels of one row and stages
+// the three input rows they need (with a one-pixel halo, zero outside the
+// image) and all the weights in shared memory, each pixel's and each weight
+// row's channels padded by 8 so that a warp's fragment loads hit 32
+// distinct banks.  Warp w computes pixels 16 w .. 16 w + 15 of the block:
+// lane (group g, thread t) reads the A fragment rows g and g + 8 (pixels) at
+// channels 2t, 2t + 1 and 2t + 8, 2t + 9 of each 16-channel chunk, and the
+// B fragment column g (output channel) at the same channel offsets.
+// Epilogue by mode: bias + ReLU to bfloat16, bias to fp32, or zeroed where
+// mask <= 0 (the ReLU derivative) to bfloat16.
+constexpr int kConvPix = kConvWarps * 16;
+
 template <int CINP, int COUTP, int MODE>
 __global__ void __launch_bounds__(kConvWarps * 32) k_conv(const uint32_t *__restrict__ in,
                                                           const uint32_t *__restrict__ wt,
                                                           const float *__restrict__ bias,
                                                           const __nv_bfloat16 *__restrict__ mask,
-                                                          void *__restrict__ out, Geometry g, int tiles_x)
+                                                          void *__restrict__ out, Geometry g, int blocks_x)
 {
     static_assert(CINP % 16 == 0 && COUTP % 8 == 0, "channel padding");
     constexpr int NT = COUTP / 8;
-    const int lane = threadIdx.x & 31;
-    const long long warp = (long long)blockIdx.x * kConvWarps + (threadIdx.x >> 5);
-    const long long rows = (long long)g.B * g.H;
-    if (warp >= rows * tiles_x) return;  // uniform per warp
-    const long long row = warp / tiles_x;
-    const int x0 = (int)(warp - row * tiles_x) * 16;
+    constexpr int XW = (CINP + 8) / 2;  // words per staged pixel
+    constexpr int WW = (CINP + 8) / 2;  // words per staged weight row
+    constexpr int NPX = kConvPix + 2;   // staged pixels per row
+    constexpr int CH16 = CINP / 8;      // 16-byte chunks per pixel
+    __shared__ __align__(16) uint32_t xs[3 * NPX * XW];
+    __shared__ __align__(16) uint32_t ws[9 * COUTP * WW];
+    const long long row = blockIdx.x / blocks_x;  // b * H + y
+    const int xb = (int)(blockIdx.x - row * blocks_x) * kConvPix;
     const int y = (int)(row % g.H);
     const long long rbase = row * g.W;
+    for (int i = threadIdx.x; i < 3 * NPX * CH16; i += blockDim.x) {
+        const int r = i / (NPX * CH16), rem = i - r * NPX * CH16;
+        const int px = rem / CH16, q = rem - px * CH16;
+        const int yy = y + r - 1, xx = xb + px - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W)
+            v = reinterpret_cast<const uint4 *>(in)[(rbase + (long long)(r - 1) * g.W + xx) * CH16 + q];
+        uint32_t *d = xs + (r * NPX + px) * XW + q * 4;
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+    }
+    for (int i = threadIdx.x; i < 9 * COUTP * (CINP / 2); i += blockDim.x) {
+        const int wr = i / (CINP / 2);
+        ws[wr * WW + (i - wr * (CINP / 2))] = wt[i];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = xb + warp * 16;
+    if (x0 >= g.W) return;  // after the only barrier
     const int grp = lane >> 2, tig = lane & 3;
     float acc[NT][4];
 #pragma unroll
     for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll 1
+#pragma unroll
     for (int ky = 0; ky < 3; ++ky) {
-        const int yy = y + ky - 1;
-        const bool rowok = yy >= 0 && yy < g.H;
-        const long long rb = rbase + (long long)(ky - 1) * g.W;
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) {
             const int tap = ky * 3 + kx;
-            const int xa = x0 + grp + kx - 1, xb = xa + 8;
-            const bool oka = rowok && xa >= 0 && xa < g.W, okb = rowok && xb >= 0 && xb < g.W;
-            const long long pa = (rb + xa) * CINP, pb = (rb + xb) * CINP;
+            // staged pixel warp * 16 + m + kx holds image column x0 + m + kx - 1
+            const uint32_t *xa = xs + (ky * NPX + warp * 16 + grp + kx) * XW;
+            const uint32_t *xc = xa + 8 * XW;
 #pragma unroll
             for (int c = 0; c < CINP / 16; ++c) {
-                const int k0 = c * 16 + tig * 2;
-                const uint32_t a0 = oka ? in[(pa + k0) >> 1] : 0u;
-                const uint32_t a1 = okb ? in[(pb + k0) >> 1] : 0u;
-                const uint32_t a2 = oka ? in[(pa + k0 + 8) >> 1] : 0u;
-                const uint32_t a3 = okb ? in[(pb + k0 + 8) >> 1] : 0u;
+                const int kw = c * 8 + tig;  // word of channels c * 16 + 2 t, + 1
+                const uint32_t a0 = xa[kw], a1 = xc[kw], a2 = xa[kw + 4], a3 = xc[kw + 4];
 #pragma unroll
                 for (int j = 0; j < NT; ++j) {
-                    const int wrow = (tap * COUTP + j * 8 + grp) * CINP;
-                    mma_bf16(acc[j], a0, a1, a2, a3, wt[(wrow + k0) >> 1], wt[(wrow + k0 + 8) >> 1]);
+                    const uint32_t *wrow = ws + (tap * COUTP + j * 8 + grp) * WW;
+                    mma_bf16(acc[j], a0, a1, a2, a3, wrow[kw], wrow[kw + 4]);
                 }
             }
         }
     }
+    const long long rb = rbase;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int xm = x0 + grp + 8 * h;
         if (xm >= g.W) continue;
-        const long long pix = rbase + xm;
+        const long long pix = rb + xm;
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
             const int ch = j * 8 + tig * 2;
@@ -348,10 +373,9 @@ template <int CINP, int COUTP, int MODE>
 cudaError_t conv(const void *in, const void *wt, const float *bias, const void *mask, void *out, const Geometry &g,
                  cudaStream_t st)
 {
-    const int tiles_x = (g.W + 15) / 16;
-    const long long warps = (long long)g.B * g.H * tiles_x;
-    k_conv<CINP, COUTP, MODE><<<blocks_of(warps, kConvWarps), kConvWarps * 32, 0, st>>>(
-        (const uint32_t *)in, (const uint32_t *)wt, bias, (const __nv_bfloat16 *)mask, out, g, tiles_x);
+    const int blocks_x = (g.W + kConvPix - 1) / kConvPix;
+    k_conv<CINP, COUTP, MODE><<<(unsigned)((long long)g.B * g.H * blocks_x), kConvWarps * 32, 0, st>>>(
+        (const uint32_t *)in, (const uint32_t *)wt, bias, (const __nv_bfloat16 *)mask, out, g, blocks_x);
     return cudaGetLastError();
 }
 
