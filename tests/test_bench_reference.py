@@ -21,3 +21,16 @@ def test_reference_arm_prints_one_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_clock_summary_parses_nvidia_smi_lines():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["2070, 2070, 800.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "2055, 2070, 812.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2062.5, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    assert bench.ClockSampler(0).summary()["samples"] == 0
