@@ -56,13 +56,9 @@ def pack(layers) -> np.ndarray:
 
 
 def init_params(seed: int) -> np.ndarray:
-    """He-normal weights, zero biases (float32), from a seeded generator."""
-    rng = np.random.default_rng(seed)
-    layers = []
-    for ci, co in LAYERS:
-        W = rng.normal(0.0, np.sqrt(2.0 / (ci * 9)), (co, ci, 3, 3))
-        layers.append((W, np.zeros(co)))
-    return pack(layers).astype(np.float32)
+    """The seeded initial parameters (from the shared input generators)."""
+    import synth
+    return synth.network_params(seed, LAYERS)
 
 
 # ---------------------------------------------------------------- bfloat16

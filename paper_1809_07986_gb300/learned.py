@@ -24,14 +24,10 @@ W, H, D = 384, 128, 64
 
 
 def init_params(seed: int) -> np.ndarray:
-    """He-normal weights and zero biases in the parameter order of the C ABI
-    (layer by layer: weights (out, in, 3, 3), then the bias)."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for ci, co in ((4, 32), (32, 32), (32, 32), (32, 6)):
-        parts.append(rng.normal(0.0, np.sqrt(2.0 / (ci * 9)), co * ci * 9))
-        parts.append(np.zeros(co))
-    theta = np.concatenate(parts).astype(np.float32)
+    """Seeded initial parameters in the order of the C ABI (He-normal weights,
+    zero biases), from the shared seeded generators."""
+    import synth
+    theta = synth.network_params(seed)
     assert theta.size == B.RSGM_CNN_PARAMS
     return theta
 

@@ -323,3 +323,16 @@ def kitti_like_sequence(seed: int, n_frames: int = 100, width: int = 1242, heigh
             tv[k] = t1.to(torch.float32)
     return dict(left=left, right=right, disp=disp, R=Rm, t=tv, K=rig.K(), baseline=baseline, rig=rig,
                 max_disp=128)
+
+
+def network_params(seed: int, layers=((4, 32), (32, 32), (32, 32), (32, 6))):
+    """Seeded initial parameters of a stack of 3x3 layers: He-normal weights
+    (std sqrt(2 / (9 in))) and zero biases, flat float32, layer by layer with
+    the weights in (out, in, ky, kx) order followed by the bias."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in layers:
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (ci * 9)), co * ci * 9))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
