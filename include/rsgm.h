@@ -225,6 +225,19 @@ int rsgm_default_detect_params(rsgm_detect_params *p);
  */
 int rsgm_detect(rsgm_stream s, const rsgm_detect_params *p, rsgm_box *boxes, int32_t capacity, int32_t *counts);
 
+/*
+ * The grouping step of the box detection (Section 4) on caller-supplied
+ * boxes, on the CPU (no device work).  `in` holds n boxes in window order
+ * (host).  While some pair has IoU > iou_num / iou_den, compared exactly on
+ * integer areas, the pair of highest IoU is replaced by its bounding box in
+ * the place of the first; ties go to the first pair (i, j).  Boxes smaller
+ * than min_area are then dropped.
+ * out: host, up to `capacity` boxes in order; *count: the number kept (may
+ * exceed capacity).  rsgm_detect groups each stream's windows this way.
+ */
+int rsgm_group_boxes(const rsgm_box *in, int32_t n, int32_t iou_num, int32_t iou_den, int32_t min_area,
+                     rsgm_box *out, int32_t capacity, int32_t *count);
+
 /* Stage timing.  While enabled, every frame records CUDA events on the
  * handle's stream around its stages: RSGM_STAGE_PREDICT (splat, hole fill,
  * reset, window), _SCAN (cell offsets), _CENSUS, _COST, _AGGREGATE (all path

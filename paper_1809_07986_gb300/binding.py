@@ -103,6 +103,8 @@ SIGNATURES = {
     "rsgm_median": (ctypes.c_int, [_P, _P]),
     "rsgm_default_detect_params": (ctypes.c_int, [ctypes.POINTER(rsgm_detect_params)]),
     "rsgm_detect": (ctypes.c_int, [_P, ctypes.POINTER(rsgm_detect_params), _P, ctypes.c_int32, _P]),
+    "rsgm_group_boxes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_enable_stage_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "rsgm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_window_offsets_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
@@ -279,6 +281,18 @@ def rsgm_detect(h: int, params: rsgm_detect_params, batch: int, capacity: int = 
     counts = np.zeros(batch, np.int32)
     _check(lib().rsgm_detect(h, ctypes.byref(params), _ptr(boxes), capacity, _ptr(counts)), "rsgm_detect")
     return [boxes[b, :min(int(counts[b]), capacity)].copy() for b in range(batch)], counts
+
+
+def rsgm_group_boxes(boxes, iou_num: int = 0, iou_den: int = 1, min_area: int = 0):
+    """Groups (x0, y0, x1, y1) boxes given in window order (on the CPU);
+    returns the kept boxes as an (m, 4) int32 array."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(boxes, np.int32).reshape(-1, 4))
+    out = np.zeros((max(len(a), 1), 4), np.int32)
+    cnt = ctypes.c_int32()
+    _check(lib().rsgm_group_boxes(_ptr(a) if len(a) else None, len(a), iou_num, iou_den, min_area, _ptr(out),
+                                  len(a), ctypes.byref(cnt)), "rsgm_group_boxes")
+    return out[:cnt.value].copy()
 
 
 def rsgm_enable_stage_timing(h: int, enable: bool = True):

@@ -163,24 +163,86 @@ struct Groups {
 // order of the merges (a merge that another order's final partition keeps
 // apart would make two of its non-overlapping final boxes overlap), and each
 // group ends at the position of its first window.  So the greedy result is
-// this fixpoint, computed by rounds of sort-and-sweep overlap detection and
-// union-find until a round merges nothing.
+// this fixpoint, computed by rounds of overlap detection and union-find
+// until a round merges nothing.
+//
+// Overlap detection: two half-open boxes share area exactly when they cover
+// a common cell of the grid whose lines are every box's edges (coordinate
+// compression); each round paints every box's cells, joining it with the
+// cell's first owner.  A box without area covers no cell and never merges,
+// as its IoU is 0.  When that grid would be too large for the box count, a
+// sort-and-sweep over x finds the pairs instead.
+// The sorted distinct x and y edges of the boxes with area.
+void grid_lines(const std::vector<Box> &v, std::vector<int> &xs, std::vector<int> &ys)
+{
+    xs.clear();
+    ys.clear();
+    for (const Box &b : v) {
+        if (b.x1 <= b.x0 || b.y1 <= b.y0) continue;
+        xs.push_back(b.x0);
+        xs.push_back(b.x1);
+        ys.push_back(b.y0);
+        ys.push_back(b.y1);
+    }
+    std::sort(xs.begin(), xs.end());
+    xs.erase(std::unique(xs.begin(), xs.end()), xs.end());
+    std::sort(ys.begin(), ys.end());
+    ys.erase(std::unique(ys.begin(), ys.end()), ys.end());
+}
+
+bool unite_by_grid(const std::vector<Box> &v, const std::vector<int> &xs, const std::vector<int> &ys, Groups &gr)
+{
+    const int n = (int)v.size();
+    const long long cw = (long long)xs.size() - 1, ch = (long long)ys.size() - 1;
+    std::vector<int> owner((size_t)(cw * ch), -1);
+    bool merged = false;
+    auto at = [](const std::vector<int> &a, int c) { return (long long)(std::lower_bound(a.begin(), a.end(), c) - a.begin()); };
+    for (int i = 0; i < n; ++i) {
+        const Box &b = v[i];
+        if (b.x1 <= b.x0 || b.y1 <= b.y0) continue;
+        const long long cx0 = at(xs, b.x0), cx1 = at(xs, b.x1), cy0 = at(ys, b.y0), cy1 = at(ys, b.y1);
+        for (long long cy = cy0; cy < cy1; ++cy)
+            for (long long cx = cx0; cx < cx1; ++cx) {
+                int &o = owner[(size_t)(cy * cw + cx)];
+                if (o < 0)
+                    o = i;
+                else
+                    merged |= gr.unite(o, i);
+            }
+    }
+    return merged;
+}
+
+bool unite_by_sweep(const std::vector<Box> &v, Groups &gr)
+{
+    const int n = (int)v.size();
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return v[a].x0 < v[b].x0; });
+    bool merged = false;
+    for (int s = 0; s < n; ++s) {
+        const Box &a = v[order[s]];
+        if (a.x1 <= a.x0 || a.y1 <= a.y0) continue;
+        for (int t = s + 1; t < n && v[order[t]].x0 < a.x1; ++t) {
+            const Box &b = v[order[t]];
+            if (b.x1 <= b.x0 || b.y1 <= b.y0) continue;
+            if (b.y0 < a.y1 && a.y0 < b.y1) merged |= gr.unite(order[s], order[t]);
+        }
+    }
+    return merged;
+}
+
 void merge_overlapping(std::vector<Box> &v)
 {
+    std::vector<int> xs, ys;
     for (;;) {
         const int n = (int)v.size();
-        std::vector<int> order(n);
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(), [&](int a, int b) { return v[a].x0 < v[b].x0; });
         Groups gr(n);
-        bool merged = false;
-        for (int s = 0; s < n; ++s) {
-            const Box &a = v[order[s]];
-            for (int t = s + 1; t < n && v[order[t]].x0 < a.x1; ++t) {
-                const Box &b = v[order[t]];
-                if (b.y0 < a.y1 && a.y0 < b.y1) merged |= gr.unite(order[s], order[t]);
-            }
-        }
+        grid_lines(v, xs, ys);
+        if (xs.size() < 2) return;  // no box has area: nothing overlaps
+        const long long cells = ((long long)xs.size() - 1) * ((long long)ys.size() - 1);
+        const bool merged =
+            cells <= std::max(1LL << 22, 256LL * n) ? unite_by_grid(v, xs, ys, gr) : unite_by_sweep(v, gr);
         if (!merged) return;
         // groups in the order of their first window; each is its members' bounding box
         std::vector<Box> next;
@@ -253,20 +315,10 @@ cudaError_t launch_detect_windows(const Buffers &b, const Geometry &g, const Det
     return cudaGetLastError();
 }
 
-// Boxes of one stream (host): the flagged windows in window order, grouped
-// (Section 4), then boxes under min_area dropped.
-int group_boxes(const uint8_t *flags, const DetectPlan &dp, int iou_num, int iou_den, long long min_area,
-                int32_t *out, int capacity)
+// Groups boxes given in window order (Section 4), then drops those under
+// min_area; writes up to `capacity` boxes and returns the number kept.
+int group_box_list(std::vector<Box> &v, int iou_num, int iou_den, long long min_area, int32_t *out, int capacity)
 {
-    std::vector<Box> v;
-    for (int s = 0; s < dp.nsizes; ++s) {
-        for (int i = 0; i < dp.ny[s] * dp.nx[s]; ++i) {
-            if (!flags[dp.first[s] + i]) continue;
-            const int iy = i / dp.nx[s], ix = i - iy * dp.nx[s];
-            const int x0 = ix * dp.stride, y0 = dp.y_min + iy * dp.stride;
-            v.push_back(Box{x0, y0, x0 + dp.size[s][0], y0 + dp.size[s][1]});
-        }
-    }
     if (iou_num == 0)
         merge_overlapping(v);
     else
@@ -285,4 +337,33 @@ int group_boxes(const uint8_t *flags, const DetectPlan &dp, int iou_num, int iou
     return n;
 }
 
+// Boxes of one stream (host): the flagged windows in window order, grouped.
+int group_boxes(const uint8_t *flags, const DetectPlan &dp, int iou_num, int iou_den, long long min_area,
+                int32_t *out, int capacity)
+{
+    std::vector<Box> v;
+    for (int s = 0; s < dp.nsizes; ++s) {
+        for (int i = 0; i < dp.ny[s] * dp.nx[s]; ++i) {
+            if (!flags[dp.first[s] + i]) continue;
+            const int iy = i / dp.nx[s], ix = i - iy * dp.nx[s];
+            const int x0 = ix * dp.stride, y0 = dp.y_min + iy * dp.stride;
+            v.push_back(Box{x0, y0, x0 + dp.size[s][0], y0 + dp.size[s][1]});
+        }
+    }
+    return group_box_list(v, iou_num, iou_den, min_area, out, capacity);
+}
+
 }  // namespace rsgm
+
+extern "C" int rsgm_group_boxes(const rsgm_box *in, int32_t n, int32_t iou_num, int32_t iou_den, int32_t min_area,
+                                rsgm_box *out, int32_t capacity, int32_t *count)
+{
+    if (!count || n < 0 || capacity < 0 || (n > 0 && !in) || (capacity > 0 && !out))
+        return rsgm::record_error(RSGM_ERR_INVALID_ARG, "NULL or negative box array argument");
+    if (iou_den < 1 || iou_num < 0 || min_area < 0)
+        return rsgm::record_error(RSGM_ERR_INVALID_ARG, "iou_den >= 1, iou_num >= 0 and min_area >= 0 required");
+    std::vector<rsgm::Box> v((size_t)n);
+    for (int32_t i = 0; i < n; ++i) v[(size_t)i] = rsgm::Box{in[i].x0, in[i].y0, in[i].x1, in[i].y1};
+    *count = rsgm::group_box_list(v, iou_num, iou_den, min_area, reinterpret_cast<int32_t *>(out), capacity);
+    return RSGM_OK;
+}

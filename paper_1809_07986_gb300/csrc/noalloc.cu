@@ -6,9 +6,6 @@
 
 #include "rsgm_internal.cuh"
 
-namespace rsgm {
-int record_error(int code, const char *msg);
-}
 
 namespace {
 

@@ -125,6 +125,9 @@ struct LearnedBuffers {
     float *loss;
 };
 
+// Records msg as the calling thread's last error (rsgm_last_error) and returns code.
+int record_error(int code, const char *msg);
+
 long long cnn_param_offset(int layer);
 cudaError_t cnn_pack(const CnnWeights &w, cudaStream_t st);
 // Inputs, the four layers and the decision of the latest prediction.
