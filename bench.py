@@ -34,12 +34,19 @@ METRIC = "frames/s and cost-cell updates/s at 1242x375 vs plain form; p99 latenc
 # direction): + C, two + P1, three min (d, d-1, d+1 against m + P2), - m, the
 # running minimum for the next pixel, + into S.
 OPS_PER_CELL_PATH = 9
+# Whole-frame algorithmic work (the scope table's per-pixel and per-cell
+# figures): 23 B per pixel (2 B images, 8 B state read, 8 B state write, 4 B
+# disparity, 1 B mask) and 4 B per cell (S written once, read once by the
+# winner-takes-all); 10 integer operations per cell and path (two neighbour
+# loads, three minima, three additions/subtractions, the running minimum, the
+# addition into S) plus 2 per cost (xor, popcount).
+FRAME_BYTES_PER_PIXEL = 23
+FRAME_BYTES_PER_CELL = 4
+FRAME_OPS_PER_CELL = 10 * N_PATHS + 2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of the
-# dominant kernel, from the ncu capture in profiles/k_paths_kitti_b32.md: one
-# 32-stream launch, 4.021 GB for 202.0 M cells (the cells of that step are
-# the mean over the run's timed steps).  The traffic reported is this figure
-# times the launch's cells.  None once the kernel changes without a new
-# capture.
+# dominant kernel, from one ncu capture of a 32-stream launch (4.021 GB for
+# 202.0 M cells).  The traffic reported is this figure times the launch's
+# cells; None once the kernel changes without a new capture.
 NCU_DRAM_BYTES_PER_CELL = 19.91
 
 
@@ -62,6 +69,8 @@ def parse():
                          "it with the fixed half-width 8 on held-out pairs")
     ap.add_argument("--serve", action="store_true",
                     help="also run the request loop: 32 Poisson streams (10-30 Hz) of 640x480/1242x375/1920x1080")
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="host cores for the oracle legs (0: every core this process may run on)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-form, latency, e2e and CPU-baseline legs")
     return ap.parse_args()
@@ -171,62 +180,118 @@ def make_inputs(seeds, nframes, device):
 
 # ------------------------------------------------------------------ reference arm: the oracle
 
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    import numpy as np
+def _reference_stream(job):
+    """Reference-arm worker: renders its own seeded stream, runs frame 0 at
+    full range and W warm-up frames untimed, then times K reduced frames."""
+    seed, warmup, steps, radius = job
     import oracle
     import synth
-    n = 1 + args.warmup + args.steps
-    s = synth.kitti_like_sequence(1000, n_frames=max(100, n), width=W, height=H, f=F, baseline=BASE,
+    n = 1 + warmup + steps
+    s = synth.kitti_like_sequence(seed, n_frames=max(100, n), width=W, height=H, f=F, baseline=BASE,
                                   render_frames=n)
-    P = oracle.Params(W, H, max_disp=D, radius=args.radius)
+    P = oracle.Params(W, H, max_disp=D, radius=radius)
     L, R = s["left"].numpy(), s["right"].numpy()
     o = oracle.frame(P, L[0], R[0])
-    times, cells = [], 0
+    total, cells = 0.0, 0
     for k in range(1, n):
         t0 = time.perf_counter()
         o = oracle.frame(P, L[k], R[k], state=(o["d"], o["p"]),
                          motion=(s["R"][k].numpy(), s["t"][k].numpy(), s["K"].numpy(), BASE))
         dt = time.perf_counter() - t0
-        if k > args.warmup:
-            times.append(dt)
+        if k > warmup:
+            total += dt
             cells += o["ncells"]
-    total = sum(times)
-    fps = len(times) / total
-    sample = "one 1242x375 stream, reduced frames %d..%d (r=%d, 8 paths), single thread" % (
-        args.warmup + 1, n - 1, args.radius)
+    return steps, total, cells
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    cores = args.cpu_cores or host_cores()
+    jobs = [(1000 + b, args.warmup, args.steps, args.radius) for b in range(cores)]
+    with mp.get_context("spawn").Pool(cores, initializer=_single_thread_worker) as pool:
+        res = pool.map(_reference_stream, jobs)
+    fps = sum(n / t for n, t, _ in res)
+    cups = sum(c * N_PATHS / t for _, t, c in res)
+    ms = 1e3 * max(t / n for n, t, _ in res)
+    sample = ("%d single-threaded oracle processes, one per host core, each on its own seeded 1242x375 stream: "
+              "reduced frames %d..%d (r=%d, 8 paths) timed; nproc=%d" % (
+                  cores, args.warmup + 1, args.warmup + args.steps, args.radius, cores))
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic",
             "config": {"workload": "kitti-shaped stereo 1242x375, D=128, r=%d, 8 paths" % args.radius,
-                       "streams": 1, "sample": sample},
-            "cell_updates_per_s": cells * N_PATHS / total,
-            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+                       "streams": cores, "sample": sample},
+            "cell_updates_per_s": cups,
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(args, left, right, Rm, tv, K, budget_s=12.0):
-    """The oracle as it stands, timed on this host on stream 0 of the workload."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _single_thread_worker():
+    """Pool initializer: one thread per oracle process (the renderer's torch
+    and numpy would otherwise start a thread per core in every process)."""
+    for k in ("OMP_NUM_THREADS", "MKL_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        os.environ[k] = "1"
+    import torch
+    torch.set_num_threads(1)
+
+
+def _oracle_stream(job):
+    """One oracle worker: frame 0 at full range (untimed), then reduced frames
+    until the budget is spent; returns (frames, seconds, cells)."""
+    L, R, Rm, tv, K, radius, budget_s = job
     import oracle
-    P = oracle.Params(W, H, max_disp=D, radius=args.radius)
-    L = left[:, 0].cpu().numpy()
-    R = right[:, 0].cpu().numpy()
+    P = oracle.Params(W, H, max_disp=D, radius=radius)
     o = oracle.frame(P, L[0], R[0])
-    times = []
-    k = 1
-    t_start = time.perf_counter()
-    while k < L.shape[0] and (time.perf_counter() - t_start < budget_s or len(times) < 3):
+    n, total, cells = 0, 0.0, 0
+    for k in range(1, L.shape[0]):
         t0 = time.perf_counter()
-        o = oracle.frame(P, L[k], R[k], state=(o["d"], o["p"]),
-                         motion=(Rm[k, 0].numpy(), tv[k, 0].numpy(), K.numpy(), BASE))
-        times.append(time.perf_counter() - t0)
-        k += 1
-    fps = len(times) / sum(times)
-    return {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": "stream 0, reduced frames 1..%d (r=%d, 8 paths), single thread" % (len(times), args.radius)}
+        o = oracle.frame(P, L[k], R[k], state=(o["d"], o["p"]), motion=(Rm[k], tv[k], K, BASE))
+        total += time.perf_counter() - t0
+        n += 1
+        cells += o["ncells"]
+        if total >= budget_s and n >= 3:
+            break
+    return n, total, cells
+
+
+def cpu_baseline(args, left, right, Rm, tv, K, budget_s=8.0, max_frames=16):
+    """The oracle as it stands, on this host's cores: single-threaded on
+    stream 0, then one single-threaded oracle process per core, each on a
+    stream of its own (the oracle itself stays plain and serial)."""
+    import multiprocessing as mp
+    import numpy as np
+    nf = min(max_frames, left.shape[0])
+    Kn = K.numpy()
+
+    def job(b):
+        return (np.ascontiguousarray(left[:nf, b].cpu().numpy()), np.ascontiguousarray(right[:nf, b].cpu().numpy()),
+                Rm[:nf, b].numpy(), tv[:nf, b].numpy(), Kn, args.radius, budget_s)
+
+    n1, t1, _ = _oracle_stream(job(0))
+    single = n1 / t1
+    cores = args.cpu_cores or host_cores()
+    jobs = [job(b % left.shape[1]) for b in range(cores)]
+    # spawn, not fork: the parent holds a CUDA context
+    with mp.get_context("spawn").Pool(cores, initializer=_single_thread_worker) as pool:
+        res = pool.map(_oracle_stream, jobs)
+    allcore = sum(n / t for n, t, _ in res)
+    return {"value": allcore, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "one single-threaded oracle process per host core (%d), each on its own stream of the "
+                      "workload: frame 0 full range untimed, then up to %d reduced frames (r=%d, 8 paths) or "
+                      "%.0f s; nproc=%d" % (cores, nf - 1, args.radius, budget_s, cores),
+            "single_thread": {"value": single, "unit": "frames/s", "frames": n1,
+                              "sample": "stream 0, reduced frames 1..%d, one thread" % n1}}
 
 
 # ------------------------------------------------------------------ mixed-resolution group
@@ -446,20 +511,42 @@ def run_ours(args, rank, world, local_rank):
     cells_per_frame = (c_after - c_before) / max(st_frames, 1)
     agg_ms = st_ms["aggregate"] / max(st_frames, 1)
     total_ms = sum(st_ms.values()) / max(st_frames, 1)
-    pk = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    # Derived integer peak: 152 SMs x 128 32-bit integer lanes x max SM clock.
-    int_peak_tops = 152 * 128 * sm_max * 1e6 / 1e12
+    # measured integer peaks of this device (the ALU roofline's denominator)
+    with torch.cuda.stream(stream):
+        int_peaks = {name: rs.rsgm_measure_int_peak(kind, stream) / 1e12
+                     for kind, name in enumerate(rs.PEAK_NAMES)}
+    int32_peak = min(int_peaks["i32_add"], int_peaks["i32_min"])
     achieved_tops = OPS_PER_CELL_PATH * cells_per_frame * N_PATHS / (agg_ms / 1e3) / 1e12
     result["stage_ms_per_step"] = {k: v / max(st_frames, 1) for k, v in st_ms.items()}
+    result["int_peaks_tops"] = dict(int_peaks, note="measured by rsgm_measure_int_peak on this GPU (scalar operations "
+                                                    "per second; a packed 16-bit-pair instruction counts two)")
     result["roofline"] = {"kernel": "k_paths (all 8 directions, one launch)", "bound": "alu", "achieved": achieved_tops,
-                          "peak": int_peak_tops, "unit": "Tops/s", "frac": achieved_tops / int_peak_tops,
+                          "peak": int32_peak, "unit": "Tops/s", "frac": achieved_tops / int32_peak,
+                          "frac_of_packed16_peak": achieved_tops / int_peaks["u16x2_mix"],
                           "traffic": (NCU_DRAM_BYTES_PER_CELL * cells_per_frame
                                       if NCU_DRAM_BYTES_PER_CELL else None),
                           "traffic_unit": "bytes per launch (ncu per-cell figure of a 32-stream launch x this launch's cells)",
-                          "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_max,
+                          "peak_source": "measured: int32 add/min throughput (the slower of the two), "
+                                         "rsgm_measure_int_peak",
                           "ops_per_cell_path": OPS_PER_CELL_PATH,
                           "share_of_step": agg_ms / total_ms if total_ms else None}
+    # whole frame: max(algorithmic bytes / HBM peak, integer ops / integer peak) / measured time
+    pk = peaks()
+    hbm = float(pk.get("hbm_gbs", 6783.5))
+    px_step = B * W * H
+    cells_step = result["cells_per_frame"] * B
+    bytes_step = FRAME_BYTES_PER_PIXEL * px_step + FRAME_BYTES_PER_CELL * cells_step
+    ops_step = FRAME_OPS_PER_CELL * cells_step
+    t_bytes = bytes_step / (hbm * 1e9) * 1e3
+    t_ops = ops_step / (int32_peak * 1e12) * 1e3
+    result["frame_roofline"] = {"bytes_per_step": bytes_step, "int_ops_per_step": ops_step,
+                                "t_bytes_ms": t_bytes, "t_int_ms": t_ops, "roofline_ms": max(t_bytes, t_ops),
+                                "measured_ms": result["ms_per_step"],
+                                "frac": max(t_bytes, t_ops) / result["ms_per_step"],
+                                "frac_packed16": max(t_bytes, ops_step / (int_peaks["u16x2_mix"] * 1e12) * 1e3)
+                                / result["ms_per_step"],
+                                "hbm_peak_gbs": hbm, "int_peak_tops": int32_peak,
+                                "counts": "23 B/pixel + 4 B/cell; 82 integer ops/cell (10 per path x 8 + 2 per cost)"}
 
     if not args.no_extras:
         # ---- e2e through the C ABI with host buffers (pinned), copies in the
@@ -560,11 +647,25 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(result), flush=True)
 
 
+def launch_ranks(n: int) -> int:
+    """Runs this script as n ranks (one per GPU) under torch.distributed.run
+    when it was started without a launcher; returns the launcher's status."""
+    port = str(29500 + os.getpid() % 1000)
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", port, os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    launched = "WORLD_SIZE" in os.environ
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if not launched and args.gpus > 1:
+        sys.exit(launch_ranks(args.gpus))
+    if world != args.gpus:
+        raise SystemExit("bench.py: --gpus %d but the launcher started %d ranks" % (args.gpus, world))
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

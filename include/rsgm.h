@@ -384,6 +384,28 @@ int rsgm_attach_cnn(rsgm_stream s, rsgm_cnn c);
  */
 int rsgm_cnn_train_step(rsgm_cnn c, rsgm_stream s, const float *d_target, float lr, float *loss);
 
+/*
+ * Integer throughput of the current device, measured: every SM runs 16
+ * independent chains per thread of one integer instruction, timed with CUDA
+ * events on cuda_stream (NULL = legacy default stream), best of three
+ * launches of several milliseconds each.  *ops_per_s receives scalar
+ * operations per second; a packed instruction on two 16-bit lanes counts as
+ * two.  The aggregation of Eq. 1 (Section 2.2) is additions and minima on
+ * small unsigned losses, so these rates are the ceiling of its integer work:
+ *   RSGM_PEAK_I32_ADD    32-bit add
+ *   RSGM_PEAK_I32_MIN    32-bit unsigned minimum
+ *   RSGM_PEAK_U16X2_MIN  minimum of two packed 16-bit lanes
+ *   RSGM_PEAK_U16X2_MIX  alternating packed minimum and 32-bit add (a
+ *                        carry-free add of two 16-bit lanes), Eq. 1's mix
+ * Allocates nothing; synchronises cuda_stream.  Unknown kind or NULL
+ * ops_per_s: RSGM_ERR_INVALID_ARG.
+ */
+#define RSGM_PEAK_I32_ADD 0
+#define RSGM_PEAK_I32_MIN 1
+#define RSGM_PEAK_U16X2_MIN 2
+#define RSGM_PEAK_U16X2_MIX 3
+int rsgm_measure_int_peak(int kind, void *cuda_stream, double *ops_per_s);
+
 /* Waits for the handle's enqueued work; reports deferred device errors. */
 int rsgm_sync(rsgm_stream s);
 

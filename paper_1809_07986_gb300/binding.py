@@ -45,6 +45,12 @@ RSGM_BUF_CNN_OUTPUT = 12
 RSGM_BUF_RADIUS = 13
 RSGM_BUF_R_MEAS = 14
 
+RSGM_PEAK_I32_ADD = 0
+RSGM_PEAK_I32_MIN = 1
+RSGM_PEAK_U16X2_MIN = 2
+RSGM_PEAK_U16X2_MIX = 3
+PEAK_NAMES = ("i32_add", "i32_min", "u16x2_min", "u16x2_mix")
+
 RSGM_STAGE_PREDICT = 0
 RSGM_STAGE_SCAN = 1
 RSGM_STAGE_CENSUS = 2
@@ -120,6 +126,7 @@ SIGNATURES = {
     "rsgm_cnn_destroy": (ctypes.c_int, [_P]),
     "rsgm_attach_cnn": (ctypes.c_int, [_P, _P]),
     "rsgm_cnn_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "rsgm_measure_int_peak": (ctypes.c_int, [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "rsgm_sync": (ctypes.c_int, [_P]),
     "rsgm_destroy_stream": (ctypes.c_int, [_P]),
     "rsgm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -389,6 +396,16 @@ def rsgm_cnn_train_step(c: int, h: int, d_target, lr: float, want_loss: bool = T
     _check(lib().rsgm_cnn_train_step(c, h, _ptr(d_target), float(lr), ctypes.byref(loss) if want_loss else None),
            "rsgm_cnn_train_step")
     return loss.value if want_loss else None
+
+
+def rsgm_measure_int_peak(kind: int, cuda_stream=None) -> float:
+    """Measured integer operations per second of the current device (see
+    include/rsgm.h); synchronises the stream."""
+    if cuda_stream is not None and hasattr(cuda_stream, "cuda_stream"):
+        cuda_stream = cuda_stream.cuda_stream
+    v = ctypes.c_double()
+    _check(lib().rsgm_measure_int_peak(kind, cuda_stream, ctypes.byref(v)), "rsgm_measure_int_peak")
+    return v.value
 
 
 def rsgm_sync(h: int):

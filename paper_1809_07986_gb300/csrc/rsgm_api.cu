@@ -684,6 +684,41 @@ int rsgm_stage_times(rsgm_stream s, double *ms, int32_t *frames)
     return RSGM_OK;
 }
 
+int rsgm_measure_int_peak(int kind, void *cuda_stream, double *ops_per_s)
+{
+    if (!ops_per_s || kind < RSGM_PEAK_I32_ADD || kind > RSGM_PEAK_U16X2_MIX)
+        return fail(RSGM_ERR_INVALID_ARG, "unknown peak kind %d or NULL output", kind);
+    *ops_per_s = 0.0;
+    int dev = 0, sms = 0;
+    RSGM_CUDA(cudaGetDevice(&dev));
+    RSGM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int blocks = sms * peak_blocks_per_sm();
+    const int iters = 1 << 15;  // several milliseconds per launch at the expected rates
+    cudaEvent_t e0, e1;
+    RSGM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(RSGM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    float best = 0.0f;
+    cudaError_t e = launch_peak(kind, blocks, iters, st);  // warm-up
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        float ms = 0.0f;
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess || (e = launch_peak(kind, blocks, iters, st)) != cudaSuccess ||
+            (e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+            break;
+        if (best == 0.0f || ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "integer peak launch");
+    if (!(best > 0.0f)) return fail(RSGM_ERR_CUDA, "integer peak: no time measured");
+    *ops_per_s = peak_ops(kind, blocks, iters) / (best * 1e-3);
+    return RSGM_OK;
+}
+
 int rsgm_sync(rsgm_stream s)
 {
     if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");

@@ -167,6 +167,11 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
 cudaError_t launch_update(const Buffers &b, const Geometry &g, const FrameParams &fp, const float *r_map, int nplanes,
                           int plane_bytes, cudaStream_t st);
 
+// Integer-throughput microbenchmark (the ALU roofline's denominator).
+cudaError_t launch_peak(int kind, int blocks, int iters, cudaStream_t st);
+double peak_ops(int kind, int blocks, int iters);
+int peak_blocks_per_sm();
+
 // After the path (Section 2.3 median output, Section 4 boxes).
 cudaError_t launch_median3(const float *d, float *out, const Geometry &g, cudaStream_t st);
 cudaError_t launch_detect_windows(const Buffers &b, const Geometry &g, const DetectPlan &dp, cudaStream_t st);
