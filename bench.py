@@ -44,10 +44,9 @@ FRAME_BYTES_PER_PIXEL = 23
 FRAME_BYTES_PER_CELL = 4
 FRAME_OPS_PER_CELL = 10 * N_PATHS + 2
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of the
-# dominant kernel, from one ncu capture of a 32-stream launch (4.021 GB for
-# 202.0 M cells).  The traffic reported is this figure times the launch's
-# cells; None once the kernel changes without a new capture.
-NCU_DRAM_BYTES_PER_CELL = 19.91
+# dominant kernel from one ncu capture; None while the kernel has changed
+# since the last capture.
+NCU_DRAM_BYTES_PER_CELL = None
 
 
 def parse():
@@ -59,7 +58,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=32, help="camera streams per GPU")
     ap.add_argument("--radius", type=int, default=4)
     ap.add_argument("--schedule", type=int, default=0,
-                    help="aggregation lines per warp for every handle (0: autotune each handle)")
+                    help="path-sweep register capacity in cells for every handle (0: autotune each handle)")
     ap.add_argument("--handles", type=int, default=2,
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
     ap.add_argument("--mixed", action="store_true",
@@ -346,7 +345,7 @@ def mixed_group(args, dev, stream):
     nstreams = sum(g[0] for g in MIXED)
     return {"frames_per_s": nstreams * args.steps / el, "ms_per_tick": 1e3 * el / args.steps,
             "streams": "6x640x480/D64 + 6x1242x375/D128 + 4x1920x1080/D256",
-            "graph_launches_per_tick": 1, "lines_per_warp_tuned": tuned}
+            "graph_launches_per_tick": 1, "sweep_capacity_tuned": tuned}
 
 
 # ------------------------------------------------------------------ request loop
@@ -490,7 +489,7 @@ def run_ours(args, rank, world, local_rank):
                          "l2": "per-step working set (ragged volumes) larger than L2"},
               "cell_updates_per_s": cells_all * N_PATHS / elapsed,
               "cells_per_frame": cells_local / (B * steps),
-              "lines_per_warp_tuned": tuned,
+              "sweep_capacity_tuned": tuned,
               "handles": "%d handles of %s streams on %d CUDA streams" % (
                   nh, "/".join(str(cut[i + 1] - cut[i]) for i in range(nh)), nh),
               "gpu_launches": 8 * steps * nh,

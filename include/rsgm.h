@@ -113,7 +113,9 @@ int rsgm_default_params(rsgm_params *p, int32_t width, int32_t height);
  * device buffer the path needs at its worst case (every pixel searching the
  * whole range): about B*W*H*(3*D + 70) bytes.  cuda_stream is a cudaStream_t
  * (NULL = the legacy default stream); all later work of the handle is
- * enqueued on it.  Requires B*W*H*D < 2^32.  On error *out is set to NULL.
+ * enqueued on it.  Requires B*W*H*round4(D) < 2^32, round4(D) = D rounded up
+ * to a multiple of 4 (each pixel's window is stored as a 4-aligned run of
+ * cells).  On error *out is set to NULL.
  */
 int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream);
 
@@ -154,11 +156,13 @@ int rsgm_set_state(rsgm_stream s, const float *disp, const float *var);
 #define RSGM_BUF_CENSUS_L 0   /* uint64 per pixel */
 #define RSGM_BUF_CENSUS_R 1   /* uint64 per pixel */
 #define RSGM_BUF_WINDOW 2     /* uint32 per pixel: lo | (width << 16) */
-#define RSGM_BUF_OFFSET 3     /* uint32 per pixel: first cell of the pixel's window */
+#define RSGM_BUF_OFFSET 3     /* uint32 per pixel: first cell of the pixel's window in the
+                                 RSGM_BUF_COST / _AGGREGATED layout (prefix sum of the widths) */
 #define RSGM_BUF_CLASS 4      /* uint8 per pixel: 0 predicted, 1 discontinuity reset, 2 no prediction */
 #define RSGM_BUF_D_PRED 5     /* float per pixel: predicted disparity (undefined where class 2) */
 #define RSGM_BUF_P_PRED 6     /* float per pixel: predicted variance (undefined where class 2) */
-#define RSGM_BUF_COST 7       /* uint8 per cell, N cells: ragged cost volume */
+#define RSGM_BUF_COST 7       /* uint8 per cell, N cells: ragged cost volume, pixels' windows
+                                 back to back in raster order */
 #define RSGM_BUF_AGGREGATED 8 /* uint16 per cell: S, the sum over enabled paths of Eq. 1 */
 #define RSGM_BUF_D_MEAS 9     /* float per pixel: sub-pixel measurement d_z */
 #define RSGM_BUF_INNOVATION 10 /* float per pixel: d_z - d_pred (0 where class 2) */
@@ -234,7 +238,11 @@ int rsgm_detect(rsgm_stream s, const rsgm_detect_params *p, rsgm_box *boxes, int
  * than min_area are then dropped.
  * out: host, up to `capacity` boxes in order; *count: the number kept (may
  * exceed capacity).  rsgm_detect groups each stream's windows this way.
+ * Every coordinate must lie in [-RSGM_BOX_COORD_LIMIT, RSGM_BOX_COORD_LIMIT]
+ * (so that areas and the exact IoU comparisons cannot overflow); otherwise
+ * RSGM_ERR_INVALID_ARG.
  */
+#define RSGM_BOX_COORD_LIMIT (1 << 20)
 int rsgm_group_boxes(const rsgm_box *in, int32_t n, int32_t iou_num, int32_t iou_den, int32_t min_area,
                      rsgm_box *out, int32_t capacity, int32_t *count);
 
@@ -273,11 +281,14 @@ int rsgm_stage_times(rsgm_stream s, double *ms, int32_t *frames);
  * default stream); nothing is allocated.
  *
  * Scratch: a fixed 512 KiB array of device memory inside the library (row
- * totals and row bases for up to 65536 rows), held on every GPU that loads
- * the library until the process exits.  rows > 65536 is rejected with
- * RSGM_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (with that device current); make that first call before
- * any stream capture.  Every call shares the one array: calls that overlap
+ * totals and row bases for up to 65536 rows), held on every GPU where the
+ * library's device code has been loaded, until the process exits.  rows >
+ * 65536 is rejected with RSGM_ERR_INVALID_ARG.  The first call on a device
+ * looks up the array's device address (with that device current).  Under
+ * CUDA's lazy module loading (the default) that lookup is also what loads the
+ * library's device code on that device and places the array, which takes
+ * device memory: a caller that reserves all device memory up front must make
+ * this first call before reserving it, and before any stream capture.  Every call shares the one array: calls that overlap
  * on the GPU (different streams, no ordering between them) race and give
  * wrong offsets.  Each call writes every scratch entry it reads, so no
  * clearing is needed between calls.
@@ -286,18 +297,20 @@ int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t 
                                 uint32_t *offsets, uint32_t *total, void *cuda_stream);
 
 /*
- * Schedule autotuner.  Times the aggregation kernel (Eq. 1) on the handle's
- * latest frame with each candidate schedule -- 1, 2, 4, ... path lines per
- * warp -- and keeps the fastest for later frames (written to *lines_per_warp
- * if not NULL).
+ * Schedule autotuner.  The aggregation kernel walks one path line per lane;
+ * a lane keeps windows of up to a "register capacity" of cells in registers
+ * and leaves wider ones to its whole warp.  rsgm_autotune times the kernel
+ * on the handle's latest frame with each capacity (2, 6, 10, 18 cells) and
+ * keeps the fastest for later frames (written to *cells if not NULL).
  * Results do not depend on the choice; only speed does.  Requires a
  * processed frame; synchronises.
  */
-int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp);
+int rsgm_autotune(rsgm_stream s, int32_t *cells);
 
-/* Sets the aggregation schedule by hand: 0 = automatic, else path lines per
- * warp (capped at what the lanes allow).  Results do not depend on it. */
-int rsgm_set_schedule(rsgm_stream s, int32_t lines_per_warp);
+/* Sets the register capacity by hand: 0 = the radius mode's default
+ * (2 radius + 1 for fixed windows), else 1 .. 32 cells, rounded up to the
+ * nearest of 2, 6, 10, 18.  Results do not depend on it. */
+int rsgm_set_schedule(rsgm_stream s, int32_t cells);
 
 /*
  * A group advances several handles of possibly different geometry by one

@@ -329,8 +329,8 @@ def rsgm_autotune(h: int) -> int:
     return n.value
 
 
-def rsgm_set_schedule(h: int, lines_per_warp: int):
-    _check(lib().rsgm_set_schedule(h, lines_per_warp), "rsgm_set_schedule")
+def rsgm_set_schedule(h: int, cells: int):
+    _check(lib().rsgm_set_schedule(h, cells), "rsgm_set_schedule")
 
 
 def rsgm_group_create(handles) -> int:

@@ -6,40 +6,30 @@
 // of a path.  Each enabled direction writes its own plane of L_r; the update
 // kernel sums the planes into S.
 //
-// All enabled directions run in one launch; a warp walks 32/G path lines, G
-// lanes per line for the common window width (see sweep below).
+// One lane walks one path line; a warp walks 32 adjacent parallel lines in
+// lockstep, so for vertical and diagonal directions its lanes visit 32
+// consecutive pixels of one image row at every step (coalesced metadata,
+// cost and plane accesses).  Losses are held as two 16-bit values per 32-bit
+// register and combined with packed minima and carry-free 32-bit additions.
 #include "rsgm_internal.cuh"
 
 namespace rsgm {
 namespace {
 
-constexpr int kWarpsPerBlock = 4;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kInf = 0x7FFF;  // larger than any loss; + P1 still fits an int
+// +inf of a packed pair.  Every finite loss is at most census bits + P2
+// (< 0x1000); a cell past the end of its window carries a cost of at least
+// 0xFF, or 0x4000 with the general masking, so its loss exceeds every cap
+// m + P2, and inf + P1 still fits 16 bits: no operation carries or borrows
+// across the two halves.
+constexpr unsigned kInf2 = 0x40004000u;
+constexpr int kWideIters = (RSGM_MAX_DISP + 127) / 128;  // 4 cells per lane per pass over a wide window
 
-// Start pixel (x, y) and length n of line j of direction (dx, dy).
-__device__ __forceinline__ void line_start(int dx, int dy, int j, int W, int H, int &x, int &y, int &n)
+__device__ __forceinline__ unsigned vmin2(unsigned a, unsigned b)
 {
-    if (dy == 0) {  // horizontal: one line per row
-        y = j;
-        x = dx > 0 ? 0 : W - 1;
-        n = W;
-    } else if (dx == 0) {  // vertical: one line per column
-        x = j;
-        y = dy > 0 ? 0 : H - 1;
-        n = H;
-    } else if (j < W) {
-        // diagonal: lines start on the row the direction enters from ...
-        x = j;
-        y = dy > 0 ? 0 : H - 1;
-        n = min(dx > 0 ? W - j : j + 1, H);
-    } else {
-        // ... then on the column it enters from (the row-start line covers the corner)
-        const int k = j - W;  // 0 .. H-2
-        y = dy > 0 ? k + 1 : k;
-        x = dx > 0 ? 0 : W - 1;
-        n = min(W, dy > 0 ? H - y : y + 1);
-    }
+    unsigned r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
 }
 
 __host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, int H)
@@ -47,169 +37,277 @@ __host__ __device__ __forceinline__ int lines_per_stream(int dx, int dy, int W, 
     return dy == 0 ? H : (dx == 0 ? W : W + H - 1);
 }
 
-constexpr int kV = 3;   // cells per lane for narrow pixels
-constexpr int kVW = 4;  // cells per lane for wide pixels
-constexpr int kPad = 6; // uint16 padding between the lines' buffers: 3 banks apart
-
-// uint16 elements of shared memory per line: two buffers of D losses + padding.
-__host__ __device__ __forceinline__ int line_stride(int D) { return 2 * D + kPad; }
-
-// Eq. 1 for kN consecutive cells d0 .. d0+kN-1 of one pixel (cells k0 + v of
-// its window, up to w): the predecessor's losses at d0-1 .. d0+kN come from
-// its buffer `prv` (+inf outside [plo, plo + pw)); cap = m + P2 (0 on the
-// first pixel of a path), sub = m.  Writes the losses to `cur` and the plane,
-// returns their minimum.
-template <int kN, typename T>
-__device__ __forceinline__ unsigned cells(const uint8_t *cst, T *pl, const uint16_t *prv, uint16_t *cur,
-                                          int d0, int k0, int w, int plo, int pw, int cap, int sub, int P1)
+// Eq. 1 for two cells (one packed pair): lft / rgt hold the predecessor's
+// losses at d-1 and d+1 of each cell (two slots each, starting one slot apart
+// from the pair), c the costs; cap2 = m + P2 and m2 = m in both halves.
+__device__ __forceinline__ unsigned eq1(unsigned lft, unsigned rgt, unsigned c, unsigned P1x2, unsigned cap2,
+                                        unsigned m2)
 {
-    int pv[kN + 2];
-#pragma unroll
-    for (int t = 0; t < kN + 2; ++t) {
-        const int dd = d0 - 1 + t;
-        pv[t] = (unsigned)(dd - plo) < (unsigned)pw ? (int)prv[dd] : kInf;
-    }
-    unsigned m = kInf;
-#pragma unroll
-    for (int v = 0; v < kN; ++v) {
-        // computed unconditionally; only the stores and the minimum are
-        // predicated, so the body has no branches
-        const int L = (int)cst[v] + min(min(pv[v + 1], cap), min(pv[v], pv[v + 2]) + P1) - sub;
-        const bool in = k0 + v < w;
-        if (in) {
-            cur[d0 + v] = (uint16_t)L;
-            pl[v] = (T)L;
-        }
-        m = in ? min(m, (unsigned)L) : m;
-    }
-    return m;
+    const unsigned ctr = __byte_perm(lft, rgt, 0x5432);  // the predecessor at d
+    unsigned t = vmin2(lft, rgt) + P1x2;
+    t = vmin2(vmin2(t, ctr), cap2);
+    return c + t - m2;  // t >= m in both halves: no borrow
 }
 
-// Walks NS = 32 / G path lines of direction (dx, dy) with one warp.
-//
-// Narrow pixels (window width <= G * kV) are handled by the line's segment of
-// G lanes, kV consecutive cells per lane.  Wide pixels (the full-range
-// windows of discontinuity resets and pixels without a prediction) are
-// handled afterwards by the whole warp, one pixel at a time, kVW cells per
-// lane.  The predecessor's losses sit in a per-line shared buffer indexed by
-// absolute disparity.  The direction is a run-time value so that one copy of
-// this code serves all eight (a copy per direction overflows the instruction
-// cache).  Metadata is fetched two pixels ahead, narrow pixels' costs one
-// pixel ahead.  The lines' buffers are padded apart by three banks: adjacent
-// lines read similar disparities at the same time.
-//
-// Loads and the first chunk of a wide pixel run without conditions (the
-// cost volume is padded for the over-reads; cells outside a window are
-// neither stored nor counted): guarded loads cost more issue slots than the
-// loads themselves.  The segment minimum comes from shuffles: a masked
-// reduction with a different mask per segment runs once per segment.
-// GT > 0 fixes the lanes per line G at compile time; 0 takes G_rt.
-template <typename T, int GT>
-__device__ __forceinline__ void sweep(int dx, int dy, int G_rt, int NS, long long line0,
-                                      const uint8_t *__restrict__ cost, T *__restrict__ plane,
-                                      const uint2 *__restrict__ meta, const Geometry &g, int P1, int P2,
-                                      uint16_t *wbuf)
+// Cells at or past the window width w get a cost of at least 0x4000 (the
+// general masking): per half, 0x8000 + slot - w has bit 15 set iff slot >= w.
+__device__ __forceinline__ unsigned mask_pair(unsigned c, unsigned slots, unsigned w2)
 {
-    const int G = GT > 0 ? GT : G_rt;
-    const int lane = threadIdx.x & 31;
-    const int seg = lane / G;  // >= NS for the idle lanes above NS * G
-    const int sl = lane - seg * G;
-    const int kb = sl * kV;    // first window cell of this lane (narrow pixels)
-    const int cap_n = G * kV;  // widest narrow window
-    const int nl = lines_per_stream(dx, dy, g.W, g.H);
-    // source lanes of the segment's other values (segments of at most 4 lanes)
-    const int src1 = seg * G + (sl + 1) % G, src2 = seg * G + (sl + 2) % G, src3 = seg * G + (sl + 3) % G;
-    const long long line = line0 + seg;
-    int n = 0;
-    const uint2 *mp = meta;
-    if (seg < NS && line < (long long)g.B * nl) {
-        const int b = (int)(line / nl);
-        const int j = (int)(line - (long long)b * nl);
-        int x, y;
-        line_start(dx, dy, j, g.W, g.H, x, y, n);
-        mp = meta + (long long)b * g.HW + (long long)y * g.W + x;
+    const unsigned x = (slots | 0x80008000u) - w2;
+    return c | ((x >> 1) & 0x40004000u);
+}
+
+// Packs the low bytes of four 16-bit losses into one word of an 8-bit plane.
+__device__ __forceinline__ unsigned pack4(unsigned a, unsigned b) { return __byte_perm(a, b, 0x6420); }
+
+// n packed pairs of the band starting at slot t (any parity): slot s lives in
+// half (s + pad) & 1 of word (s + pad) >> 1.
+template <int N>
+__device__ __forceinline__ void band_load(const unsigned *band, int t, int pad, unsigned (&u)[N])
+{
+    const int s = t + pad;
+    const unsigned *p = band + (s >> 1);
+    const unsigned sel = (s & 1) ? 0x5432u : 0x3210u;
+    unsigned w0 = p[0];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const unsigned w1 = p[i + 1];
+        u[i] = __byte_perm(w0, w1, sel);
+        w0 = w1;
     }
-    const int nmax = (int)__reduce_max_sync(kFull, (unsigned)n);
-    const int step = dy * g.W + dx;
-    uint16_t *bufA = wbuf + min(seg, NS - 1) * line_stride(g.D);
-    uint16_t *bufB = bufA + g.D;
+}
 
-    uint2 mc = n > 0 ? mp[0] : make_uint2(0u, 0u);
-    uint2 mn = n > 1 ? mp[step] : make_uint2(0u, 0u);
-    uint8_t cc[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) cc[v] = cost[mc.x + kb + v];
-    int plo = 0, pw = 0, pmin = 0;
-    // unrolled by two so that the fetched-ahead registers swap roles instead
-    // of being copied (a copy would wait for the fetch to land)
-#pragma unroll 2
-    for (int i = 0; i < nmax; ++i) {
-        mp += step;
-        const uint2 mnn = (i + 2 < n) ? mp[step] : make_uint2(0u, 0u);
-        uint8_t cn[kV];
-#pragma unroll
-        for (int v = 0; v < kV; ++v) cn[v] = cost[mn.x + kb + v];
-        const unsigned o = mc.x;
-        const int lo = (int)(mc.y & 0xFFFFu);
-        const int w = i < n ? (int)(mc.y >> 16) : 0;
-        const int sel = i & 1;
-        const int cap = i == 0 ? 0 : pmin + P2;
+// Walks 32 adjacent lines of one direction.
+//
+// Narrow pixels (window width <= 2 NR) are done by the line's own lane, the
+// window in NR packed registers: slot k holds the loss at d = lo + k.  When
+// the window moves by at most 2 against the predecessor's, the predecessor's
+// losses are realigned in registers; otherwise they go through the lane's
+// band in shared memory.  Wide pixels (the full-range windows of resets and
+// pixels without a prediction) are done by the whole warp, 4 cells per lane,
+// with the predecessor's losses in the line's band.  A band holds a window at
+// slots [0, w) with +inf on [-pad, 0) and on [round4(w), round4(w) + pad);
+// reads that can see no slot of [0, w) take +inf without loading.
+//
+// Metadata is fetched two steps ahead and narrow costs one step ahead.
+template <typename T, int NR, bool kCheap>
+__device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok, const uint8_t *__restrict__ cost,
+                                     T *__restrict__ plane, const uint2 *__restrict__ meta, const LinePlan &plan,
+                                     unsigned *band_all, unsigned *band)
+{
+    constexpr int NC = 2 * NR;        // narrow capacity in cells
+    constexpr int NW = (NR + 1) / 2;  // cost words of a narrow window
+    const Geometry &g = plan.g;
+    const int lane = threadIdx.x & 31;
+    const int W = g.W, H = g.H, pad = plan.pad;
 
-        unsigned lmin = kInf;
-        if (w <= cap_n && kb < w)
-            lmin = cells<kV, T>(cc, plane + o + kb, sel ? bufA : bufB, sel ? bufB : bufA, lo + kb, kb, w, plo, pw,
-                                cap, pmin, P1);
-        if (G == 32) {
-            lmin = __reduce_min_sync(kFull, lmin);
-        } else if (G <= 4) {
-            // every lane gathers its segment's other G - 1 values
-            const unsigned l0 = lmin;
-            lmin = min(lmin, __shfl_sync(kFull, l0, src1));
-            if (G > 2) lmin = min(lmin, __shfl_sync(kFull, l0, src2));
-            if (G > 3) lmin = min(lmin, __shfl_sync(kFull, l0, src3));
+    // this lane's active steps [s_first, s_last] and its pixel at step 0
+    int s_first = 0, s_last = -1;
+    long long gi0 = 0;
+    if (line_ok) {
+        if (dy == 0) {
+            s_last = W - 1;
+            gi0 = (long long)b * g.HW + (long long)k * W + (dx > 0 ? 0 : W - 1);
         } else {
-            for (int off = 1; off < G; off <<= 1) {
-                const unsigned y = __shfl_down_sync(kFull, lmin, off);
-                if (sl + off < G) lmin = min(lmin, y);
+            gi0 = (long long)b * g.HW + (long long)(dy > 0 ? 0 : H - 1) * W + k;
+            if (dx == 0) {
+                s_last = H - 1;
+            } else if (dx > 0) {
+                s_first = max(0, -k);
+                s_last = min(H - 1, W - 1 - k);
+            } else {
+                s_first = max(0, k - (W - 1));
+                s_last = min(H - 1, k);
             }
-            lmin = __shfl_sync(kFull, lmin, seg * G);
+        }
+    }
+    const bool any = s_first <= s_last;
+    const int s0 = (int)__reduce_min_sync(kFull, any ? (unsigned)s_first : 0x7FFFFFFFu);
+    const int s1 = (int)__reduce_max_sync(kFull, any ? (unsigned)s_last : 0u);
+    if (s0 > s1) return;  // no lane of this warp has a pixel (uniform)
+    const long long step = (long long)dy * W + dx;
+    auto active = [&](int s) { return s >= s_first && s <= s_last; };
+    auto meta_at = [&](int s) { return active(s) ? meta[gi0 + s * step] : make_uint2(0u, 0u); };
+
+    const unsigned P1x2 = (unsigned)plan.P1 * 0x10001u;
+    unsigned P[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) P[i] = kInf2;
+    int plo = 0, pw = 0, pm = 0;  // predecessor window and minimum; pw = 0: no predecessor
+    bool inband = false;          // the predecessor's losses are in the band, not in P
+
+    uint2 mc = meta_at(s0), mn = meta_at(s0 + 1);
+    unsigned cc[NW];
+    {
+        const int w = (int)(mc.y >> 16);
+        const unsigned *src = (const unsigned *)(cost + mc.x);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) cc[q] = (w > 0 && w <= NC) ? src[q] : 0u;
+    }
+#pragma unroll 2
+    for (int s = s0; s <= s1; ++s) {
+        const uint2 mnn = meta_at(s + 2);
+        unsigned cn[NW];
+        {
+            const int w = (int)(mn.y >> 16);
+            const unsigned *src = (const unsigned *)(cost + mn.x);
+#pragma unroll
+            for (int q = 0; q < NW; ++q) cn[q] = (w > 0 && w <= NC) ? src[q] : 0u;
+        }
+        const unsigned o = mc.x;
+        const int lo = (int)(mc.y & 0xFFFFu), w = (int)(mc.y >> 16);
+
+        if (w > 0 && w <= NC) {
+            // ---- narrow: this lane alone
+            unsigned U[NR + 1];
+            unsigned cap2 = 0u, m2 = 0u;
+            if (pw == 0) {
+#pragma unroll
+                for (int i = 0; i <= NR; ++i) U[i] = kInf2;
+            } else {
+                cap2 = (unsigned)(pm + plan.P2) * 0x10001u;
+                m2 = (unsigned)pm * 0x10001u;
+                const int e = lo - plo - 1;  // slot of the predecessor at d - 1 for the first cell
+                if (inband || e < -3 || e > 1) {
+                    if (!inband) {
+                        // realign a large move through the band
+#pragma unroll
+                        for (int i = 0; i < NR; ++i) band[(pad >> 1) + i] = P[i];
+                        for (int q = 0; q < (pad >> 1); ++q) band[(pad >> 1) + NR + q] = kInf2;
+                    }
+                    if (e >= pw || e + NC + 1 < 0) {
+#pragma unroll
+                        for (int i = 0; i <= NR; ++i) U[i] = kInf2;
+                    } else {
+                        band_load<NR + 1>(band, e, pad, U);
+                    }
+                } else {
+                    // e = 2 sh + odd with sh in {-2, -1, 0}: U[i] = Q[i + sh],
+                    // Q[j] = predecessor slots (2j + odd, 2j + odd + 1)
+                    const unsigned sel = (e & 1) ? 0x5432u : 0x3210u;
+                    const int sh = e >> 1;
+                    unsigned Q[NR + 3];  // Q[j + 2] for j = -2 .. NR
+                    Q[0] = kInf2;
+                    Q[1] = __byte_perm(kInf2, P[0], sel);
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) Q[j + 2] = __byte_perm(P[j], j + 1 < NR ? P[j + 1] : kInf2, sel);
+                    Q[NR + 2] = kInf2;
+#pragma unroll
+                    for (int i = 0; i <= NR; ++i) U[i] = sh == 0 ? Q[i + 2] : (sh == -1 ? Q[i + 1] : Q[i]);
+                }
+            }
+            unsigned cw[NW];
+#pragma unroll
+            for (int q = 0; q < NW; ++q) cw[q] = (q == 0 || 4 * q < w) ? cc[q] : 0xFFFFFFFFu;
+            const unsigned w2 = (unsigned)w * 0x10001u;
+            unsigned run = kInf2;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                unsigned c = __byte_perm(cw[i >> 1], 0u, (i & 1) ? 0x4342u : 0x4140u);
+                if (!kCheap) c = mask_pair(c, (unsigned)(2 * i) | ((unsigned)(2 * i + 1) << 16), w2);
+                P[i] = eq1(U[i], U[i + 1], c, P1x2, cap2, m2);
+                run = vmin2(run, P[i]);
+            }
+            // plane words of the pixel's cells [0, round4(w))
+            if (sizeof(T) == 1) {
+                unsigned *dst = (unsigned *)(plane + o);
+#pragma unroll
+                for (int q = 0; q < NW; ++q)
+                    if (q == 0 || 4 * q < w) dst[q] = pack4(P[2 * q], 2 * q + 1 < NR ? P[2 * q + 1] : kInf2);
+            } else {
+                uint2 *dst = (uint2 *)(plane + o);
+#pragma unroll
+                for (int q = 0; q < NW; ++q)
+                    if (q == 0 || 4 * q < w) dst[q] = make_uint2(P[2 * q], 2 * q + 1 < NR ? P[2 * q + 1] : kInf2);
+            }
+            plo = lo;
+            pw = w;
+            pm = (int)min(run & 0xFFFFu, run >> 16);
+            inband = false;
         }
 
-        // wide pixels: the whole warp, one pixel at a time
-        unsigned wide = __ballot_sync(kFull, seg < NS && sl == 0 && w > cap_n);
-        while (wide) {
-            const int src = __ffs(wide) - 1;
-            wide &= wide - 1;
-            const int s2 = src / G;
-            const unsigned f1 = __shfl_sync(kFull, (unsigned)lo | ((unsigned)plo << 16), src);
-            const unsigned f2 = __shfl_sync(kFull, (unsigned)w | ((unsigned)pw << 16), src);
-            const int pmin2 = __shfl_sync(kFull, pmin, src);
-            const unsigned o2 = __shfl_sync(kFull, o, src);
-            const int lo2 = (int)(f1 & 0xFFFFu), plo2 = (int)(f1 >> 16);
-            const int w2 = (int)(f2 & 0xFFFFu), pw2 = (int)(f2 >> 16);
-            const int cap2 = i == 0 ? 0 : pmin2 + P2;
-            uint16_t *b2 = wbuf + s2 * line_stride(g.D);
-            unsigned m2 = kInf;
-            int k0 = lane * kVW;
-            do {
-                uint8_t c4[kVW];
+        // ---- wide: the whole warp, one pixel at a time
+        unsigned wide = __ballot_sync(kFull, w > NC);
+        if (wide) {
+            if (w > NC && pw > 0 && !inband) {
 #pragma unroll
-                for (int v = 0; v < kVW; ++v) c4[v] = cost[o2 + k0 + v];
-                m2 = min(m2, cells<kVW, T>(c4, plane + o2 + k0, b2 + (sel ^ 1) * g.D, b2 + sel * g.D, lo2 + k0, k0,
-                                           w2, plo2, pw2, cap2, pmin2, P1));
-                k0 += 32 * kVW;
-            } while (k0 < w2);
-            m2 = __reduce_min_sync(kFull, m2);
-            if (seg == s2) lmin = m2;
+                for (int i = 0; i < NR; ++i) band[(pad >> 1) + i] = P[i];
+                for (int q = 0; q < (pad >> 1); ++q) band[(pad >> 1) + NR + q] = kInf2;
+            }
+            __syncwarp();
+            while (wide) {
+                const int src = __ffs(wide) - 1;
+                wide &= wide - 1;
+                const unsigned so = __shfl_sync(kFull, o, src);
+                const unsigned f1 = __shfl_sync(kFull, (unsigned)lo | ((unsigned)w << 16), src);
+                const unsigned f2 = __shfl_sync(kFull, (unsigned)plo | ((unsigned)pw << 16), src);
+                const int spm = __shfl_sync(kFull, pm, src);
+                const int slo = (int)(f1 & 0xFFFFu), sw = (int)(f1 >> 16);
+                const int splo = (int)(f2 & 0xFFFFu), spw = (int)(f2 >> 16);
+                unsigned *sb = band_all + src * plan.band_words;
+                const unsigned cap2 = spw ? (unsigned)(spm + plan.P2) * 0x10001u : 0u;
+                const unsigned m2 = spw ? (unsigned)spm * 0x10001u : 0u;
+                const unsigned w2 = (unsigned)sw * 0x10001u;
+                unsigned Lr[kWideIters][2];
+                unsigned run = kInf2;
+#pragma unroll
+                for (int it = 0; it < kWideIters; ++it) {
+                    const int c0 = 4 * lane + 128 * it;
+                    Lr[it][0] = Lr[it][1] = kInf2;
+                    if (c0 < sw) {
+                        unsigned U[3];
+                        const int t0 = slo + c0 - 1 - splo;  // predecessor slot of d - 1 for cell c0
+                        if (spw == 0 || t0 >= spw || t0 + 5 < 0) {
+                            U[0] = U[1] = U[2] = kInf2;
+                        } else {
+                            band_load<3>(sb, t0, pad, U);
+                        }
+                        const unsigned cw = *(const unsigned *)(cost + so + c0);
+                        unsigned c01 = __byte_perm(cw, 0u, 0x4140u), c23 = __byte_perm(cw, 0u, 0x4342u);
+                        if (!kCheap) {
+                            c01 = mask_pair(c01, (unsigned)c0 | ((unsigned)(c0 + 1) << 16), w2);
+                            c23 = mask_pair(c23, (unsigned)(c0 + 2) | ((unsigned)(c0 + 3) << 16), w2);
+                        }
+                        const unsigned L0 = eq1(U[0], U[1], c01, P1x2, cap2, m2);
+                        const unsigned L1 = eq1(U[1], U[2], c23, P1x2, cap2, m2);
+                        run = vmin2(run, vmin2(L0, L1));
+                        if (sizeof(T) == 1)
+                            *(unsigned *)(plane + so + c0) = pack4(L0, L1);
+                        else
+                            *(uint2 *)(plane + so + c0) = make_uint2(L0, L1);
+                        Lr[it][0] = L0;
+                        Lr[it][1] = L1;
+                    }
+                }
+                const unsigned r = __reduce_min_sync(kFull, min(run & 0xFFFFu, run >> 16));
+                __syncwarp();  // every read of the source band is done
+#pragma unroll
+                for (int it = 0; it < kWideIters; ++it) {
+                    const int c0 = 4 * lane + 128 * it;
+                    if (c0 < sw) {
+                        // two 32-bit stores: bands have an odd word stride, so
+                        // a band word is not 8-byte aligned in general
+                        sb[((c0 + pad) >> 1)] = Lr[it][0];
+                        sb[((c0 + pad) >> 1) + 1] = Lr[it][1];
+                    }
+                }
+                const int ext = (sw + 3) & ~3;
+                if (lane < (pad >> 1)) sb[((ext + pad) >> 1) + lane] = kInf2;
+                __syncwarp();
+                if (lane == src) {
+                    plo = slo;
+                    pw = sw;
+                    pm = (int)r;
+                    inband = true;
+                }
+            }
         }
-        __syncwarp();
-        pmin = (int)lmin;
-        plo = lo;
-        pw = w;
+        if (w == 0) pw = 0;  // off the image: the next pixel starts the line
+
         mc = mn;
         mn = mnn;
 #pragma unroll
-        for (int v = 0; v < kV; ++v) cc[v] = cn[v];
+        for (int q = 0; q < NW; ++q) cc[q] = cn[q];
     }
 }
 
@@ -217,51 +315,57 @@ __device__ __forceinline__ void sweep(int dx, int dy, int G_rt, int NS, long lon
 __constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 __constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
-template <typename T, int GT>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
-    k_paths(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
-            const __grid_constant__ PathPlan plan)
+template <typename T, int NR, bool kCheap>
+__global__ void __launch_bounds__(kLineWarps * 32)
+    k_lines(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
+            const __grid_constant__ LinePlan plan)
 {
-    extern __shared__ uint16_t smem[];
-    const int warp = threadIdx.x >> 5;
-    const long long gw = (long long)blockIdx.x * kWarpsPerBlock + warp;
+    extern __shared__ unsigned smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * kLineWarps + warp;
     if (gw >= plan.warp_begin[plan.ndir]) return;  // uniform per warp
-    int s = 0;
-    while (s + 1 < plan.ndir && gw >= plan.warp_begin[s + 1]) ++s;
-    const long long line0 = (gw - plan.warp_begin[s]) * plan.lines_per_warp;
-    uint16_t *wbuf = smem + warp * plan.lines_per_warp * line_stride(plan.g.D);
-    T *plane = planes + (long long)plan.plane_of[s] * plan.plane_stride;
-    const int dir = plan.dir[s];
-    sweep<T, GT>(kDX[dir], kDY[dir], plan.lanes, plan.lines_per_warp, line0, cost, plane, meta, plan.g, plan.P1,
-             plan.P2, wbuf);
+    int si = 0;
+    while (si + 1 < plan.ndir && gw >= plan.warp_begin[si + 1]) ++si;
+    const int dir = plan.dir[si];
+    const int dx = kDX[dir], dy = kDY[dir];
+    const int nl = lines_per_stream(dx, dy, plan.g.W, plan.g.H);
+    const int wps = (nl + 31) / 32;
+    const long long wi = gw - plan.warp_begin[si];
+    const int b = (int)(wi / wps), kw = (int)(wi - (long long)b * wps);
+    const int kbase = (dx > 0 && dy != 0) ? -(plan.g.H - 1) : 0;
+    const bool line_ok = kw * 32 + lane < nl;
+    unsigned *band_all = smem + warp * 32 * plan.band_words;
+    unsigned *band = band_all + lane * plan.band_words;
+    for (int q = 0; q < (plan.pad >> 1); ++q) band[q] = kInf2;  // slots [-pad, 0): always +inf
+    __syncwarp();
+    T *plane = planes + (long long)plan.plane_of[si] * plan.plane_stride;
+    walk<T, NR, kCheap>(dx, dy, b, kbase + kw * 32 + lane, line_ok, cost, plane, meta, plan, band_all, band);
 }
 
-template <typename T, int GT>
-cudaError_t launch_g(const Buffers &b, const PathPlan &plan, cudaStream_t st)
+template <typename T, int NR, bool kCheap>
+cudaError_t launch_nr(const Buffers &b, const LinePlan &plan, cudaStream_t st)
 {
     const long long warps = plan.warp_begin[plan.ndir];
     if (warps == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    const size_t smem = (size_t)kWarpsPerBlock * plan.lines_per_warp * line_stride(plan.g.D) * sizeof(uint16_t);
+    const unsigned blocks = (unsigned)((warps + kLineWarps - 1) / kLineWarps);
+    const size_t smem = (size_t)kLineWarps * 32 * plan.band_words * sizeof(unsigned);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_paths<T, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_lines<T, NR, kCheap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_paths<T, GT><<<blocks, kWarpsPerBlock * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
+    k_lines<T, NR, kCheap><<<blocks, kLineWarps * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
     return cudaGetLastError();
 }
 
-// The common lane counts (windows of 2r + 1 for r = 2 and 4; full range) are
-// compile-time constants in their own instantiations: index arithmetic on
-// G folds away, which shortens every step.
-template <typename T>
-cudaError_t launch_t(const Buffers &b, const PathPlan &plan, cudaStream_t st)
+template <typename T, bool kCheap>
+cudaError_t launch_t(const Buffers &b, const LinePlan &plan, int nr, cudaStream_t st)
 {
-    switch (plan.lanes) {
-    case 2: return launch_g<T, 2>(b, plan, st);
-    case 3: return launch_g<T, 3>(b, plan, st);
-    case 32: return launch_g<T, 32>(b, plan, st);
-    default: return launch_g<T, 0>(b, plan, st);
+    switch (nr) {
+    case 1: return launch_nr<T, 1, kCheap>(b, plan, st);
+    case 3: return launch_nr<T, 3, kCheap>(b, plan, st);
+    case 5: return launch_nr<T, 5, kCheap>(b, plan, st);
+    default: return launch_nr<T, 9, kCheap>(b, plan, st);
     }
 }
 
@@ -270,23 +374,31 @@ cudaError_t launch_t(const Buffers &b, const PathPlan &plan, cudaStream_t st)
 const int kHostDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 const int kHostDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
-int lanes_per_line(int window)
+int sweep_capacity(int cells)
 {
-    // Enough lanes (3 cells each) for the common (predicted) window, at least
-    // 2 (at most 16 lines per warp); wider windows go through the whole-warp
-    // path.
-    const int G = (window + kV - 1) / kV;
-    return G < 2 ? 2 : (G > 32 ? 32 : G);
+    // instantiated register capacities (2 NR cells): 2, 6, 10, 18
+    return cells <= 2 ? 2 : (cells <= 6 ? 6 : (cells <= 10 ? 10 : 18));
 }
 
-cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         int lanes, int plane_bytes, int sm_count, int lines_override, cudaStream_t st)
+cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2, int nbits,
+                         int plane_bytes, int capacity, cudaStream_t st)
 {
-    PathPlan plan;
+    LinePlan plan;
     plan.g = g;
     plan.P1 = P1;
     plan.P2 = P2;
     plan.plane_stride = plane_stride(g);
+    const int nr = sweep_capacity(capacity) / 2;
+    // +inf padding around a band's window: at least the widest read past it
+    // (a narrow read spans 2 NR + 2 slots), even so that slot 0 is word aligned
+    const int pad = max(6, 2 * nr + 2);
+    plan.pad = (pad + 1) & ~1;
+    // slots [-pad, round4(max(D, 2 NR)) + pad) in 32-bit words, an odd count
+    // so that the lanes' bands fall in different shared-memory banks
+    const int cap = (max(g.D, 2 * nr) + 3) & ~3;
+    int words = (cap + 2 * plan.pad) / 2;
+    if (!(words & 1)) ++words;
+    plan.band_words = words;
     // Long lines first so that the tail of the launch is short: horizontal,
     // diagonal, vertical.  Planes are numbered by direction bit order.
     static const int order[8] = {0, 1, 4, 5, 6, 7, 2, 3};
@@ -294,35 +406,21 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     for (int i = 0; i < 8; ++i) plane_index[i] = (path_mask & (1u << i)) ? np++ : -1;
     plan.ndir = 0;
     plan.warp_begin[0] = 0;
-    plan.lanes = lanes;
-    // Lines per warp.  fill = lines per warp that would give every SM 32
-    // warps; about a quarter of it (measured on paper-shaped frames at 1, 8,
-    // 32 and 64 streams) balances a warp's sequential steps against the work
-    // its lines share per step.  Capped by the lanes (32 / lanes) and by the
-    // line buffers: those of 8 resident blocks stay within 168 KB, so that a
-    // third of the SM's 256 KB L1 still caches the cost and window loads (at
-    // D = 128, 12 lines per warp ran 10% slower than 10).
-    long long total_lines = 0;
-    for (int dir = 0; dir < 8; ++dir)
-        if (path_mask & (1u << dir)) total_lines += (long long)g.B * lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H);
-    const long long fill = total_lines / ((long long)(sm_count > 0 ? sm_count : 152) * 32);
-    const long long smem_cap = (168LL * 1024 / 8) / ((long long)kWarpsPerBlock * line_stride(g.D) * 2);
-    long long most = 32 / lanes;
-    if (smem_cap < most) most = smem_cap < 1 ? 1 : smem_cap;
-    const long long pick = (fill + 2) / 4;
-    plan.lines_per_warp = (int)(pick < 1 ? 1 : (pick > most ? most : pick));
-    if (lines_override > 0) plan.lines_per_warp = (int)(lines_override < 32 / lanes ? lines_override : 32 / lanes);
-    const int lines_per_warp = plan.lines_per_warp;
-    for (int k = 0; k < 8; ++k) {
-        const int dir = order[k];
+    for (int kk = 0; kk < 8; ++kk) {
+        const int dir = order[kk];
         if (!(path_mask & (1u << dir))) continue;
-        const long long lines = (long long)g.B * lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H);
+        const long long warps = (long long)g.B * ((lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H) + 31) / 32);
         plan.dir[plan.ndir] = dir;
         plan.plane_of[plan.ndir] = plane_index[dir];
-        plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + (lines + lines_per_warp - 1) / lines_per_warp;
+        plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + warps;
         plan.ndir++;
     }
-    return plane_bytes == 1 ? launch_t<uint8_t>(b, plan, st) : launch_t<uint16_t>(b, plan, st);
+    // the cheap masking (cells past a window cost 0xFF) needs every cap
+    // m + P2 <= nbits + 2 P2 below 0xFF
+    const bool cheap = plane_bytes == 1 && nbits + 2 * P2 < 255;
+    if (plane_bytes == 1)
+        return cheap ? launch_t<uint8_t, true>(b, plan, nr, st) : launch_t<uint8_t, false>(b, plan, nr, st);
+    return launch_t<uint16_t, false>(b, plan, nr, st);
 }
 
 }  // namespace rsgm

@@ -170,8 +170,10 @@ struct Groups {
 // a common cell of the grid whose lines are every box's edges (coordinate
 // compression); each round paints every box's cells, joining it with the
 // cell's first owner.  A box without area covers no cell and never merges,
-// as its IoU is 0.  When that grid would be too large for the box count, a
-// sort-and-sweep over x finds the pairs instead.
+// as its IoU is 0.  Painting costs the cells the boxes cover, so when that
+// total exceeds the pairs a sort-and-sweep over x could check (n^2 / 2), or
+// the grid would be too large for the box count, the sweep finds the pairs
+// instead.
 // The sorted distinct x and y edges of the boxes with area.
 void grid_lines(const std::vector<Box> &v, std::vector<int> &xs, std::vector<int> &ys)
 {
@@ -241,8 +243,21 @@ void merge_overlapping(std::vector<Box> &v)
         grid_lines(v, xs, ys);
         if (xs.size() < 2) return;  // no box has area: nothing overlaps
         const long long cells = ((long long)xs.size() - 1) * ((long long)ys.size() - 1);
-        const bool merged =
-            cells <= std::max(1LL << 22, 256LL * n) ? unite_by_grid(v, xs, ys, gr) : unite_by_sweep(v, gr);
+        bool grid = cells <= std::max(1LL << 22, 256LL * n);
+        if (grid) {
+            const long long pairs = (long long)n * (n - 1) / 2;
+            long long paint = 0;
+            auto at = [](const std::vector<int> &a, int c) {
+                return (long long)(std::lower_bound(a.begin(), a.end(), c) - a.begin());
+            };
+            for (const Box &b : v) {
+                if (b.x1 <= b.x0 || b.y1 <= b.y0) continue;
+                paint += (at(xs, b.x1) - at(xs, b.x0)) * (at(ys, b.y1) - at(ys, b.y0));
+                if (paint > pairs) break;
+            }
+            grid = paint <= std::max(pairs, 4LL * n);
+        }
+        const bool merged = grid ? unite_by_grid(v, xs, ys, gr) : unite_by_sweep(v, gr);
         if (!merged) return;
         // groups in the order of their first window; each is its members' bounding box
         std::vector<Box> next;
@@ -277,8 +292,9 @@ void merge_greedy(std::vector<Box> &v, int iou_num, int iou_den)
                 const long long in = overlap(v[i], v[j]);
                 if (!in) continue;
                 const long long un = area(v[i]) + area(v[j]) - in;
-                if (in * iou_den <= (long long)iou_num * un) continue;
-                if (bi < 0 || in * best_un > best_in * un) {
+                // areas reach 2^42 for coordinates within +-2^20: compare in 128 bits
+                if ((__int128)in * iou_den <= (__int128)iou_num * un) continue;
+                if (bi < 0 || (__int128)in * best_un > (__int128)best_in * un) {
                     bi = (int)i;
                     bj = (int)j;
                     best_in = in;
@@ -362,6 +378,11 @@ extern "C" int rsgm_group_boxes(const rsgm_box *in, int32_t n, int32_t iou_num, 
         return rsgm::record_error(RSGM_ERR_INVALID_ARG, "NULL or negative box array argument");
     if (iou_den < 1 || iou_num < 0 || min_area < 0)
         return rsgm::record_error(RSGM_ERR_INVALID_ARG, "iou_den >= 1, iou_num >= 0 and min_area >= 0 required");
+    const int32_t lim = RSGM_BOX_COORD_LIMIT;
+    for (int32_t i = 0; i < n; ++i)
+        if (in[i].x0 < -lim || in[i].x0 > lim || in[i].y0 < -lim || in[i].y0 > lim || in[i].x1 < -lim ||
+            in[i].x1 > lim || in[i].y1 < -lim || in[i].y1 > lim)
+            return rsgm::record_error(RSGM_ERR_INVALID_ARG, "box coordinates must lie in [-2^20, 2^20]");
     std::vector<rsgm::Box> v((size_t)n);
     for (int32_t i = 0; i < n; ++i) v[(size_t)i] = rsgm::Box{in[i].x0, in[i].y0, in[i].x1, in[i].y1};
     *count = rsgm::group_box_list(v, iou_num, iou_den, min_area, reinterpret_cast<int32_t *>(out), capacity);

@@ -60,10 +60,19 @@ constexpr int kLaneCells = 16;  // windows up to this width are filled by their 
 // K3: one warp per 32 consecutive pixels.  Each lane finalises one pixel's
 // metadata (first cell = row base + in-row prefix, window) and writes its
 // window's costs C(p, d) = popcount(cL(x,y) ^ cR(x-d,y)), a match left of the
-// image costing every census bit.  Narrow windows (up to kLaneCells cells)
-// are filled by their own lane (neighbouring lanes read overlapping right
-// census words, which the L1 serves); wider ones by the whole warp, one pixel
-// at a time, 32 consecutive cells per pass.
+// image costing every census bit.  A window starts on a 4-cell boundary and
+// is written as whole 32-bit words, the padding cells past its width holding
+// 0xFF.  Narrow windows (up to kLaneCells cells) are filled by their own lane
+// (neighbouring lanes read overlapping right census words, which the L1
+// serves); wider ones by the whole warp, one pixel at a time, one word per
+// lane per pass.
+__device__ __forceinline__ unsigned cost_byte(unsigned long long cl, const unsigned long long *cr, int xr, int k,
+                                              int w, int nbits)
+{
+    if (k >= w) return 0xFFu;
+    return (unsigned)(xr >= 0 ? __popcll(cl ^ cr[xr]) : nbits);
+}
+
 __global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long long *__restrict__ cen_l,
                                                          const unsigned long long *__restrict__ cen_r,
                                                          const uint32_t *__restrict__ win,
@@ -92,9 +101,12 @@ __global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long lo
     const int lo = (int)(wv & 0xFFFFu), w = (int)(wv >> 16);
     const unsigned long long *cr = cen_r + row * g.W;
     if (valid && w <= kLaneCells) {
-        for (int k = 0; k < w; ++k) {
-            const int xr = x - lo - k;
-            cost[o + k] = (uint8_t)(xr >= 0 ? __popcll(cl ^ cr[xr]) : nbits);
+        unsigned *dst = (unsigned *)(cost + o);
+        for (int k0 = 0; k0 < w; k0 += 4) {
+            const int xr = x - lo - k0;
+            dst[k0 >> 2] = cost_byte(cl, cr, xr, k0, w, nbits) | (cost_byte(cl, cr, xr - 1, k0 + 1, w, nbits) << 8) |
+                           (cost_byte(cl, cr, xr - 2, k0 + 2, w, nbits) << 16) |
+                           (cost_byte(cl, cr, xr - 3, k0 + 3, w, nbits) << 24);
         }
     }
     unsigned wide = __ballot_sync(0xffffffffu, valid && w > kLaneCells);
@@ -107,9 +119,12 @@ __global__ void __launch_bounds__(kCostWarps * 32) k_cost(const unsigned long lo
         const long long r2 = __shfl_sync(0xffffffffu, row, src);
         const unsigned long long cl2 = __shfl_sync(0xffffffffu, cl, src);
         const unsigned long long *cr2 = cen_r + r2 * g.W;
-        for (int k = lane; k < w2; k += 32) {
-            const int xr = xl - k;
-            cost[o2 + k] = (uint8_t)(xr >= 0 ? __popcll(cl2 ^ cr2[xr]) : nbits);
+        unsigned *dst = (unsigned *)(cost + o2);
+        for (int k0 = 4 * lane; k0 < w2; k0 += 128) {
+            const int xr = xl - k0;
+            dst[k0 >> 2] = cost_byte(cl2, cr2, xr, k0, w2, nbits) | (cost_byte(cl2, cr2, xr - 1, k0 + 1, w2, nbits) << 8) |
+                           (cost_byte(cl2, cr2, xr - 2, k0 + 2, w2, nbits) << 16) |
+                           (cost_byte(cl2, cr2, xr - 3, k0 + 3, w2, nbits) << 24);
         }
     }
 }

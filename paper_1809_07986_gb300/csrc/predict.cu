@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
                                                 uint32_t *__restrict__ win, uint8_t *__restrict__ cls,
                                                 uint32_t *__restrict__ inrow,
                                                 uint32_t *__restrict__ row_total,
+                                                uint32_t *__restrict__ row_cells,
                                                 unsigned long long *__restrict__ key,
                                                 const uint8_t *__restrict__ radius_map, Geometry g,
                                                 FrameParams fp)
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
     const int row = blockIdx.x;  // b * H + y
     const int y = row % g.H;
     const long long rbase = (long long)row * g.W;
-    unsigned carry = 0;
+    unsigned carry = 0, cells = 0;
     for (int x0 = 0; x0 < g.W; x0 += kWinTile) {
         const int n = min(kWinTile, g.W - x0);
         for (int i = threadIdx.x; i < n + 2; i += blockDim.x) {
@@ -236,7 +237,8 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
             win[gi] = (uint32_t)lo | ((uint32_t)w << 16);
             cls[gi] = c;
             key[gi] = 0ull;
-            sw[i] = (unsigned)w;
+            sw[i] = (unsigned)round4(w);  // cells are laid out in 4-aligned runs
+            cells += (unsigned)w;
         }
         __syncthreads();
         const int j0 = threadIdx.x * kWinPer, j1 = min(j0 + kWinPer, n);
@@ -253,26 +255,35 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
         carry += total;
         __syncthreads();  // the next tile reuses sd, sw and total
     }
-    if (threadIdx.x == 0) row_total[row] = carry;
+    block_exclusive_scan(cells, total);
+    if (threadIdx.x == 0) {
+        row_total[row] = carry;
+        row_cells[row] = total;
+    }
 }
 
 // Initial frame: every pixel searches [0, D) and has no prediction.
 __global__ void __launch_bounds__(256) k_full_window(uint32_t *__restrict__ win, uint8_t *__restrict__ cls,
                                                      uint32_t *__restrict__ inrow,
-                                                     uint32_t *__restrict__ row_total, Geometry g)
+                                                     uint32_t *__restrict__ row_total,
+                                                     uint32_t *__restrict__ row_cells, Geometry g)
 {
     long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.NPIX) return;
     int x = (int)(gi % g.W);
     win[gi] = (uint32_t)g.D << 16;
     cls[gi] = 2;
-    inrow[gi] = (uint32_t)x * (uint32_t)g.D;
-    if (x == 0) row_total[gi / g.W] = (uint32_t)g.W * (uint32_t)g.D;
+    inrow[gi] = (uint32_t)x * (uint32_t)round4(g.D);
+    if (x == 0) {
+        row_total[gi / g.W] = (uint32_t)g.W * (uint32_t)round4(g.D);
+        row_cells[gi / g.W] = (uint32_t)g.W * (uint32_t)g.D;
+    }
 }
 
-// Exclusive scan of the B*H row totals in one block; records the frame's cell
-// count in the counters.
+// Exclusive scan of the B*H rounded row totals in one block (the first cell
+// of every row); records the frame's cell count in the counters.
 __global__ void __launch_bounds__(256) k_row_scan(const uint32_t *__restrict__ row_total,
+                                                  const uint32_t *__restrict__ row_cells,
                                                   uint32_t *__restrict__ row_base, int nrows,
                                                   int nstreams,
                                                   unsigned long long *__restrict__ counters)
@@ -280,17 +291,23 @@ __global__ void __launch_bounds__(256) k_row_scan(const uint32_t *__restrict__ r
     __shared__ unsigned total;
     int chunk = (nrows + blockDim.x - 1) / blockDim.x;
     int r0 = threadIdx.x * chunk, r1 = min(nrows, r0 + chunk);
-    unsigned local = 0;
-    for (int r = r0; r < r1; ++r) local += row_total[r];
+    unsigned local = 0, real = 0;
+    for (int r = r0; r < r1; ++r) {
+        local += row_total[r];
+        real += row_cells[r];
+    }
     unsigned pre = block_exclusive_scan(local, total);
+    const unsigned rounded = total;
     for (int r = r0; r < r1; ++r) {
         row_base[r] = pre;
         pre += row_total[r];
     }
+    block_exclusive_scan(real, total);
     if (threadIdx.x == 0) {
         counters[0] += (unsigned long long)nstreams;
         counters[1] += total;
         counters[2] = total;
+        counters[3] = rounded;
     }
 }
 
@@ -314,19 +331,19 @@ cudaError_t launch_window(const Buffers &b, const Geometry &g, const FrameParams
 {
     if (fp.radius_mode == RSGM_RADIUS_LEARNED && !b.radius) return cudaErrorInvalidValue;
     k_window<<<(unsigned)(g.B * g.H), 256, 0, st>>>(b.d_pred, b.p_pred, b.win, b.cls, b.inrow,
-                                                     b.row_total, b.key, b.radius, g, fp);
+                                                     b.row_total, b.row_cells, b.key, b.radius, g, fp);
     return cudaGetLastError();
 }
 
 cudaError_t launch_full_window(const Buffers &b, const Geometry &g, cudaStream_t st)
 {
-    k_full_window<<<blocks_for(g.NPIX, 256), 256, 0, st>>>(b.win, b.cls, b.inrow, b.row_total, g);
+    k_full_window<<<blocks_for(g.NPIX, 256), 256, 0, st>>>(b.win, b.cls, b.inrow, b.row_total, b.row_cells, g);
     return cudaGetLastError();
 }
 
 cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, cudaStream_t st)
 {
-    k_row_scan<<<1, 256, 0, st>>>(b.row_total, b.row_base, g.B * g.H, g.B, b.counters);
+    k_row_scan<<<1, 256, 0, st>>>(b.row_total, b.row_cells, b.row_base, g.B * g.H, g.B, b.counters);
     return cudaGetLastError();
 }
 

@@ -30,9 +30,9 @@ struct rsgm_stream_s {
     Geometry g;
     int nbits;
     int nplanes;      // enabled path directions
-    int lanes;        // lanes per path line in the aggregation kernel
+    int capacity;     // window cells a path-sweep lane keeps in registers (default for the radius mode)
     int sm_count;     // multiprocessors of the handle's device
-    int tuned_lines;  // aggregation lines per warp picked by rsgm_autotune (0: heuristic)
+    int tuned_cap;    // register capacity picked by rsgm_autotune / rsgm_set_schedule (0: default)
     bool capturing;   // enqueueing into a group's graph: no stage-timing events
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
@@ -126,9 +126,9 @@ int check_params(const rsgm_params *p)
     if (!(p->q >= 0.0f) || !(p->r_meas > 0.0f) || !(p->tau_disc >= 0.0f) || !(p->gate_gamma > 0.0f) ||
         p->p_reset != p->p_reset)
         return fail(RSGM_ERR_INVALID_ARG, "noise / threshold parameters out of range");
-    unsigned long long cells = (unsigned long long)p->batch * p->width * p->height * p->max_disp;
+    unsigned long long cells = (unsigned long long)p->batch * p->width * p->height * round4(p->max_disp);
     if (cells >= 0xFFFFFFFFull)
-        return fail(RSGM_ERR_INVALID_ARG, "batch*width*height*max_disp must be < 2^32");
+        return fail(RSGM_ERR_INVALID_ARG, "batch*width*height*round4(max_disp) must be < 2^32");
     return RSGM_OK;
 }
 
@@ -148,7 +148,7 @@ int alloc(T **ptr, size_t count, void **all, int &nall)
 void free_buffers(Buffers &b)
 {
     void *ptrs[] = {b.img_l, b.img_r, b.cen_l, b.cen_r, b.d,    b.p,    b.key,       b.d_pred,
-                    b.p_pred, b.win, b.cls,   b.inrow, b.meta, b.row_total, b.row_base, b.cost,
+                    b.p_pred, b.win, b.cls,   b.inrow, b.meta, b.row_total, b.row_base, b.row_cells, b.cost,
                     b.planes, b.S,   b.d_int, b.mask,  b.d_z,  b.nu,   b.counters, b.median,
                     b.sat,    b.flags};
     for (void *p : ptrs)
@@ -242,7 +242,8 @@ int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool c
     RSGM_MARK(s, 3);
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
-    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, s->tuned_lines, s->st));
+    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes,
+                           s->tuned_cap ? s->tuned_cap : s->capacity, s->st));
     RSGM_MARK(s, 5);
     RSGM_CUDA(launch_update(s->buf, g, fp, r_map, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
@@ -320,6 +321,57 @@ void destroy_timer(StageTimer &t)
     t.n = 0;
 }
 
+
+// The ragged volumes in their documented layout: each pixel's cells follow
+// the previous pixel's, with no padding (the device keeps 4-aligned runs).
+// Offsets are the prefix sum of the widths; costs and S are gathered run by
+// run on the host.  Synchronises.
+int read_ragged(rsgm_stream s, int which, void *dst, size_t capacity, size_t *bytes)
+{
+    const size_t n = (size_t)s->g.NPIX;
+    unsigned long long cnt[4];
+    RSGM_CUDA(cudaMemcpyAsync(cnt, s->buf.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s->st));
+    RSGM_CUDA(cudaStreamSynchronize(s->st));
+    const size_t cells = (size_t)cnt[2], padded = (size_t)cnt[3];
+    const size_t elem = which == RSGM_BUF_AGGREGATED ? 2 : (which == RSGM_BUF_COST ? 1 : 4);
+    const size_t size = which == RSGM_BUF_OFFSET ? n * 4 : cells * elem;
+    if (bytes) *bytes = size;
+    if (!dst) return RSGM_OK;
+    if (capacity < size) return fail(RSGM_ERR_INVALID_ARG, "capacity %zu < %zu bytes", capacity, size);
+    uint2 *meta = (uint2 *)malloc(n * sizeof(uint2));
+    uint8_t *vol = which == RSGM_BUF_OFFSET ? nullptr : (uint8_t *)malloc(padded * elem + 1);
+    uint8_t *out = (uint8_t *)malloc(size + 1);
+    int rc = RSGM_OK;
+    if (!meta || !out || (which != RSGM_BUF_OFFSET && !vol)) {
+        rc = fail(RSGM_ERR_OOM, "host allocation failed");
+    } else {
+        cudaError_t e = cudaMemcpyAsync(meta, s->buf.meta, n * sizeof(uint2), cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess && vol && padded)
+            e = cudaMemcpyAsync(vol, which == RSGM_BUF_COST ? (const void *)s->buf.cost : (const void *)s->buf.S,
+                                padded * elem, cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "reading a ragged volume");
+    }
+    if (rc == RSGM_OK) {
+        size_t at = 0;
+        for (size_t i = 0; i < n; ++i) {
+            const size_t w = meta[i].y >> 16;
+            if (which == RSGM_BUF_OFFSET) {
+                ((uint32_t *)out)[i] = (uint32_t)at;
+            } else if (at + w <= cells && meta[i].x + w <= padded) {
+                memcpy(out + at * elem, vol + (size_t)meta[i].x * elem, w * elem);
+            }
+            at += w;
+        }
+        cudaError_t e = cudaMemcpyAsync(dst, out, size, cudaMemcpyDefault, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copying a ragged volume out");
+    }
+    free(meta);
+    free(vol);
+    free(out);
+    return rc;
+}
 }  // namespace
 
 namespace rsgm {
@@ -358,13 +410,13 @@ int rsgm_footprint(const rsgm_params *p, uint64_t *bytes)
     int rc = check_params(p);
     if (rc) return rc;
     const uint64_t n = (uint64_t)p->batch * p->width * p->height;
-    const uint64_t cells = n * (uint64_t)p->max_disp;
+    const uint64_t cells = n * (uint64_t)round4(p->max_disp);
     const int nbits = p->census_w * p->census_h - 1;
     const uint64_t plane_bytes = nbits + p->P2 <= 255 ? 1 : 2;
     const uint64_t stride = (cells + 15) / 16 * 16;
     const uint64_t per_pixel = 2 + 16 + 8 + 8 + 8 + 4 + 1 + 4 + 8 + 2 + 1 + 4 + 4 + 4 + RSGM_MAX_WINDOW_SIZES;
     *bytes = n * per_pixel + cells * (1 + 2) + 128 + stride * __builtin_popcount(p->path_mask) * plane_bytes +
-             (uint64_t)p->batch * p->height * 8 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32 +
+             (uint64_t)p->batch * p->height * 12 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32 +
              (p->radius_mode == RSGM_RADIUS_LEARNED ? n * 261 : 0);
     return RSGM_OK;
 }
@@ -396,18 +448,19 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
     s->nbits = p->census_w * p->census_h - 1;
     s->nplanes = __builtin_popcount(p->path_mask);
     s->plane_bytes = s->nbits + p->P2 <= 255 ? 1 : 2;
-    // Lanes per line: enough for the common (predicted) window; wider windows
-    // loop.  Full-range modes use a whole warp per line.
-    // Learned windows: sized for the fallback half-width 8 (wider ones loop).
-    s->lanes = lanes_per_line(p->radius_mode == RSGM_RADIUS_FIXED     ? 2 * p->radius + 1
-                              : p->radius_mode == RSGM_RADIUS_LEARNED ? 17
-                                                                      : p->max_disp);
+    // Register capacity of a path-sweep lane: the common (predicted) window.
+    // Learned windows: the fallback half-width 8; the paper's variance rule:
+    // half-widths up to 4; full range: registers only if the whole range fits.
+    s->capacity = p->radius_mode == RSGM_RADIUS_FIXED     ? 2 * p->radius + 1
+                  : p->radius_mode == RSGM_RADIUS_LEARNED ? 17
+                  : p->radius_mode == RSGM_RADIUS_VARIANCE ? 9
+                  : (p->max_disp <= 18 ? p->max_disp : 2);
     s->p_reset = p->p_reset > 0.0f ? p->p_reset : (float)p->max_disp * (float)p->max_disp / 12.0f;
     s->has_state = false;
     memset(&s->buf, 0, sizeof(s->buf));
     Buffers &b = s->buf;
     const size_t n = (size_t)s->g.NPIX, rows = (size_t)p->batch * p->height;
-    const size_t cells = n * (size_t)p->max_disp;
+    const size_t cells = (size_t)max_cells(s->g);
     void *all[40];
     int nall = 0;
     if ((rc = alloc(&b.img_l, n, all, nall)) || (rc = alloc(&b.img_r, n, all, nall)) ||
@@ -417,7 +470,8 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc(&b.p_pred, n, all, nall)) || (rc = alloc(&b.win, n, all, nall)) ||
         (rc = alloc(&b.cls, n, all, nall)) || (rc = alloc(&b.inrow, n, all, nall)) ||
         (rc = alloc(&b.meta, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
-        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.cost, cells + 128, all, nall)) ||  // + the path sweeps' unguarded over-reads (< 128 B)
+        (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.row_cells, rows, all, nall)) ||
+        (rc = alloc(&b.cost, cells + 128, all, nall)) ||  // + the path sweep's prefetch past the last window (< 128 B)
         (rc = alloc((uint8_t **)&b.planes, (size_t)plane_stride(s->g) * s->nplanes * s->plane_bytes, all, nall)) ||
         (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
         (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
@@ -504,31 +558,13 @@ int rsgm_read_buffer(rsgm_stream s, int which, void *dst, size_t capacity, size_
     size_t n = (size_t)s->g.NPIX;
     const void *src = nullptr;
     size_t size = 0;
-    if (which == RSGM_BUF_COST || which == RSGM_BUF_AGGREGATED) {
-        unsigned long long last = 0;
-        RSGM_CUDA(cudaMemcpyAsync(&last, s->buf.counters + 2, sizeof(last), cudaMemcpyDeviceToHost, s->st));
-        RSGM_CUDA(cudaStreamSynchronize(s->st));
-        if (which == RSGM_BUF_COST) {
-            src = s->buf.cost;
-            size = (size_t)last;
-        } else {
-            src = s->buf.S;
-            size = (size_t)last * sizeof(uint16_t);
-        }
-    } else {
+    if (which == RSGM_BUF_COST || which == RSGM_BUF_AGGREGATED || which == RSGM_BUF_OFFSET)
+        return read_ragged(s, which, dst, capacity, bytes);
+    {
         switch (which) {
         case RSGM_BUF_CENSUS_L: src = s->buf.cen_l; size = n * 8; break;
         case RSGM_BUF_CENSUS_R: src = s->buf.cen_r; size = n * 8; break;
         case RSGM_BUF_WINDOW: src = s->buf.win; size = n * 4; break;
-        case RSGM_BUF_OFFSET: {
-            // first-cell field of the (first cell, window) pairs: a strided copy
-            if (bytes) *bytes = n * 4;
-            if (!dst) return RSGM_OK;
-            if (capacity < n * 4) return fail(RSGM_ERR_INVALID_ARG, "capacity %zu < %zu bytes", capacity, n * 4);
-            RSGM_CUDA(cudaMemcpy2DAsync(dst, 4, s->buf.meta, sizeof(uint2), 4, n, cudaMemcpyDefault, s->st));
-            RSGM_CUDA(cudaStreamSynchronize(s->st));
-            return RSGM_OK;
-        }
         case RSGM_BUF_CLASS: src = s->buf.cls; size = n; break;
         case RSGM_BUF_D_PRED: src = s->buf.d_pred; size = n * 4; break;
         case RSGM_BUF_P_PRED: src = s->buf.p_pred; size = n * 4; break;
@@ -913,15 +949,15 @@ int rsgm_cnn_train_step(rsgm_cnn c, rsgm_stream s, const float *d_target, float 
     return RSGM_OK;
 }
 
-int rsgm_set_schedule(rsgm_stream s, int32_t lines_per_warp)
+int rsgm_set_schedule(rsgm_stream s, int32_t cells)
 {
     if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
-    if (lines_per_warp < 0 || lines_per_warp > 32) return fail(RSGM_ERR_INVALID_ARG, "lines_per_warp in [0, 32]");
-    s->tuned_lines = lines_per_warp;
+    if (cells < 0 || cells > 32) return fail(RSGM_ERR_INVALID_ARG, "schedule (register capacity) in [0, 32]");
+    s->tuned_cap = cells ? sweep_capacity(cells) : 0;
     return RSGM_OK;
 }
 
-int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
+int rsgm_autotune(rsgm_stream s, int32_t *cells)
 {
     if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
     if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "autotuning needs a processed frame");
@@ -933,11 +969,9 @@ int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
         cudaEventDestroy(e0);
         return fail(RSGM_ERR_CUDA, "cudaEventCreate");
     }
-    // candidates: 1, 2, 4, ... up to 32 / lanes path lines per warp
-    int cands[16], nc = 0;
-    const int most = 32 / s->lanes;
-    for (int c = 1; c < most; c *= 2) cands[nc++] = c;
-    cands[nc++] = most;
+    // candidates: the instantiated register capacities
+    const int cands[4] = {2, 6, 10, 18};
+    const int nc = 4;
     int best = 0;
     float best_ms = 0.0f;
     int rc = RSGM_OK;
@@ -949,8 +983,8 @@ int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
         for (int rep = 0; rep < 3 && rc == RSGM_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, s->st);
             if (e == cudaSuccess)
-                e = launch_paths(s->buf, s->g, s->P.path_mask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes,
-                                 s->sm_count, cand, s->st);
+                e = launch_paths(s->buf, s->g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes, cand,
+                                 s->st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float t = 0.0f;
@@ -966,8 +1000,8 @@ int rsgm_autotune(rsgm_stream s, int32_t *lines_per_warp)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    s->tuned_lines = best;
-    if (lines_per_warp) *lines_per_warp = best;
+    s->tuned_cap = best;
+    if (cells) *cells = best;
     return RSGM_OK;
 }
 

@@ -15,9 +15,17 @@ struct Geometry {
     long long NPIX;  // B * HW
 };
 
+// Cell layout.  Each pixel's window of w cells starts on a multiple of 4
+// cells and occupies round4(w) cells (the ragged volume is a raster-order
+// prefix sum of the rounded widths), so that every 4 cells of a window are
+// one aligned 32-bit word of an 8-bit volume.  Cells [w, round4(w)) are
+// padding: the cost volume holds 0xFF there, the other volumes anything.
+__host__ __device__ inline int round4(int w) { return (w + 3) & ~3; }
+// Worst-case cells of a frame (every pixel searching the whole range).
+inline long long max_cells(const Geometry &g) { return g.NPIX * (long long)round4(g.D); }
 // Elements between consecutive direction planes: the worst-case cell count,
 // rounded up so that every plane starts 16-element aligned.
-inline long long plane_stride(const Geometry &g) { return (g.NPIX * (long long)g.D + 15) / 16 * 16; }
+inline long long plane_stride(const Geometry &g) { return (max_cells(g) + 15) / 16 * 16; }
 
 // Ego-motion of one stream: X_k = R X_{k-1} + t.
 struct Motion {
@@ -33,12 +41,14 @@ struct SplatArgs {
 };
 
 // Launch plan of the aggregation kernel: the enabled directions in launch
-// order, the first warp of each, and the plane each writes.
-struct PathPlan {
+// order, the first warp of each (a warp walks 32 adjacent path lines of one
+// stream), the plane each writes, and the per-lane band of shared memory.
+constexpr int kLineWarps = 4;  // warps per block of the aggregation kernel
+struct LinePlan {
     Geometry g;
     int P1, P2;
-    int lanes;           // lanes per line for narrow pixels (the common window width)
-    int lines_per_warp;  // <= 32 / lanes
+    int pad;         // +inf slots kept on both sides of a band's window
+    int band_words;  // 32-bit words of shared memory per lane
     int ndir;
     int dir[8];
     int plane_of[8];
@@ -76,14 +86,16 @@ struct Buffers {
     uint8_t *cls;                       // 0 predicted, 1 reset, 2 no prediction
     uint32_t *inrow;                    // exclusive offset within the pixel's row, NPIX
     uint2 *meta;                        // (first cell, window) of the pixel, NPIX
-    uint32_t *row_total, *row_base;     // B*H each
-    uint8_t *cost;                      // ragged cost volume, NPIX * D
-    void *planes;                       // one plane of L_r per enabled direction, NPIX * D each
-    uint16_t *S;                        // ragged aggregated cost, NPIX * D
+    uint32_t *row_total, *row_base;     // B*H each: rounded cells of the row, first cell of the row
+    uint32_t *row_cells;                // B*H: cells of the row (sum of the true widths)
+    uint8_t *cost;                      // ragged cost volume, max_cells + 128
+    void *planes;                       // one plane of L_r per enabled direction, plane_stride each
+    uint16_t *S;                        // ragged aggregated cost, max_cells
     int16_t *d_int;
     uint8_t *mask;
     float *d_z, *nu;
-    unsigned long long *counters;       // [0] frames, [1] cells, [2] cells of the last frame
+    unsigned long long *counters;       // [0] frames, [1] cells, [2] cells of the last frame,
+                                        // [3] rounded cells of the last frame
     float *median;                      // 3x3 median of d, NPIX
     unsigned long long *sat;            // integral image of |nu|, B * (H+1) * (W+1)
     uint8_t *flags;                     // detection flag per window, B * RSGM_MAX_WINDOW_SIZES * H * W
@@ -156,11 +168,12 @@ cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *le
 cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStream_t st);
 
 // Aggregation, Eq. 1 (Section 2.2): every enabled direction in one launch,
-// `lanes` lanes per path line, planes of `plane_bytes` (1 or 2) per cell.
-int lanes_per_line(int widest_narrow_window);
-// lines_override: 0 = automatic, else path lines per warp.
-cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2,
-                         int lanes, int plane_bytes, int sm_count, int lines_override, cudaStream_t st);
+// planes of `plane_bytes` (1 or 2) per cell.  Windows of up to `capacity`
+// cells (rounded up by sweep_capacity to 2, 6, 10 or 18) are walked in a
+// lane's registers, wider ones by the whole warp.
+int sweep_capacity(int cells);
+cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2, int nbits,
+                         int plane_bytes, int capacity, cudaStream_t st);
 
 // Sum of the planes, winner-takes-all, Kalman correction and gate
 // (Sections 2.2-2.4).

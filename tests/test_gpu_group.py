@@ -92,6 +92,48 @@ def test_group_matches_members_run_alone(rs, orc):
             s.close()
 
 
+def test_group_with_a_full_hd_d256_member_against_the_oracle(rs, orc):
+    # The largest geometry of the mixed-resolution batch (1920x1080, 256
+    # disparities) inside a group beside a small member; both are checked
+    # against the oracle chained over the same frames.
+    import synth
+    geoms = [(1, 1920, 1080, 256, 1000.0), (2, 160, 120, 32, 100.0)]
+    nframes = 3
+    data = []
+    for gi, (B, W, H, D, f) in enumerate(geoms):
+        seqs = [synth.kitti_like_sequence(900 + 10 * gi + b, n_frames=nframes, width=W, height=H, f=f,
+                                          baseline=0.54, device="cuda") for b in range(B)]
+        st = lambda k: torch.stack([q[k] for q in seqs])
+        data.append(dict(L=st("left"), R=st("right"), Rm=st("R").cpu(), t=st("t").cpu(), K=seqs[0]["K"].cpu()))
+    stream = torch.cuda.current_stream()
+    members = [rs.Stream(_params(rs, B, W, H, D), stream) for (B, W, H, D, f) in geoms]
+    group = rs.rsgm_group_create([m.handle for m in members])
+    try:
+        for m, x in zip(members, data):
+            m.full_frame(x["L"][:, 0].contiguous(), x["R"][:, 0].contiguous())
+        for k in range(1, nframes):
+            rs.rsgm_group_reduced_frame(group, [x["L"][:, k].contiguous() for x in data],
+                                        [x["R"][:, k].contiguous() for x in data],
+                                        [x["Rm"][:, k].contiguous() for x in data],
+                                        [x["t"][:, k].contiguous() for x in data], [x["K"] for x in data],
+                                        [0.54] * len(data))
+        for m, (B, W, H, D, f), x in zip(members, geoms, data):
+            g = read_all(rs, m)
+            op = oracle_params(orc, _params(rs, B, W, H, D))
+            for b in range(B):
+                Lb, Rb = x["L"][b].cpu().numpy(), x["R"][b].cpu().numpy()
+                o = orc.frame(op, Lb[0], Rb[0])
+                for k in range(1, nframes):
+                    o = orc.frame(op, Lb[k], Rb[k], state=(o["d"], o["p"]),
+                                  motion=(x["Rm"][b, k].numpy(), x["t"][b, k].numpy(), x["K"].numpy(), 0.54))
+                stats = compare_stream(g, b, o, H, W)
+                assert stats["bit_equal_f32"]
+    finally:
+        rs.rsgm_group_destroy(group)
+        for m in members:
+            m.close()
+
+
 def test_group_rejects_host_images_and_mixed_streams(rs):
     P = rs.rsgm_default_params(64, 32, max_disp=16)
     with rs.Stream(P) as a, rs.Stream(P, torch.cuda.Stream()) as b:

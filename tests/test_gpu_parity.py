@@ -91,6 +91,17 @@ def test_kitti_shaped_frames(rs, orc, radius):
         max(s["max_rel_p_vs_f64"] for s in stats)))
 
 
+def test_kitti_shaped_sixteen_consecutive_frames(rs, orc):
+    # One paper-shaped stream over a full-range frame and 15 reduced frames:
+    # the state carried from frame to frame (Section 2.4) stays identical to
+    # the oracle's at every frame, not only after the first prediction.
+    L, R, Rm, tv, K, b = batch_sequences([77], 16, 1242, 375, 721.0, 0.54, device="cuda")
+    P = rs.rsgm_default_params(1242, 375, max_disp=128, radius=4)
+    stats = run_sequence(rs, orc, P, L, R, Rm, tv, K, b, 16)
+    assert len(stats) == 16 and all(s["bit_equal_f32"] for s in stats)
+    assert all(s["ncells"] < stats[0]["ncells"] / 3 for s in stats[1:])
+
+
 def test_kitti_shaped_batch_in_the_benchmark_launch_configuration(rs, orc):
     # 32 streams as in the throughput benchmark; the oracle checks two of them.
     B = 32

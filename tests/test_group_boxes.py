@@ -76,3 +76,29 @@ def test_lattice_and_degenerate_boxes_match_the_oracle(rs, orc, seed):
     for iou, min_area in [((0, 1), 0), ((0, 1), 1500), ((1, 2), 0)]:
         got = rs.rsgm_group_boxes(boxes, iou[0], iou[1], min_area)
         assert np.array_equal(got, orc.merge_boxes(boxes, iou[0], iou[1], min_area)), (iou, min_area)
+
+
+def test_coordinates_beyond_the_limit_are_rejected(rs):
+    lim = 1 << 20
+    assert rs.rsgm_group_boxes(np.array([[-lim, -lim, lim, lim]], np.int32)).shape == (1, 4)
+    for bad in ([-lim - 1, 0, 10, 10], [0, 0, lim + 1, 10], [0, -2 ** 31, 10, 2 ** 31 - 1]):
+        with pytest.raises(rs.RsgmError) as e:
+            rs.rsgm_group_boxes(np.array([bad], np.int32))
+        assert e.value.code == rs.RSGM_ERR_INVALID_ARG
+
+
+def test_nested_boxes_and_extreme_areas_match_the_oracle(rs, orc):
+    import time
+    # 1000 nested boxes: a 2000 x 2000 grid whose painting would cost about
+    # 1e9 cell writes, where checking the pairs costs 5e5
+    n = 1000
+    nested = np.array([[i, i, 4000 - i, 4000 - i] for i in range(n)], np.int32)[::-1].copy()
+    t0 = time.perf_counter()
+    got = rs.rsgm_group_boxes(nested)
+    assert time.perf_counter() - t0 < 2.0
+    assert np.array_equal(got, orc.merge_boxes(nested, 0, 1, 0))
+    # areas near 2^42 with an IoU threshold: exact comparisons, no overflow
+    lim = 1 << 20
+    big = np.array([[-lim, -lim, lim, lim], [-lim + 1, -lim, lim, lim], [0, 0, lim, lim]], np.int32)
+    for iou in [(1, 2), (999999, 1000000), (1, 4)]:
+        assert np.array_equal(rs.rsgm_group_boxes(big, *iou), orc.merge_boxes(big, iou[0], iou[1], 0)), iou
