@@ -136,10 +136,34 @@ int rsgm_full_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right);
  * through (R_b, t_b), search each pixel's window, aggregate (Eq. 1), take the
  * winner, correct (Eqs. 5-6) and gate.  R: B*9 floats, t: B*3 floats, K: 9
  * floats, all host memory, copied during the call; baseline in metres (> 0).
- * Returns RSGM_ERR_NO_STATE if the handle has no state yet.
+ * Returns RSGM_ERR_NO_STATE if some stream of the handle has no state yet.
  */
 int rsgm_reduced_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right,
                        const float *R, const float *t, const float *K, float baseline);
+
+/*
+ * One frame in which each of the handle's B streams ("slots") has its own
+ * role, for serving many camera streams from one handle: a slot's stream
+ * advances only when its next frame has arrived, and a slot freed by a
+ * finished stream takes a new stream, which starts with a full-range frame.
+ *   RSGM_SLOT_IDLE     the stream does not advance: no cells are searched
+ *                      and its state and per-pixel outputs stay as they are
+ *   RSGM_SLOT_REDUCED  a frame of the method, exactly as rsgm_reduced_frame
+ *   RSGM_SLOT_FULL     an initial frame, exactly as rsgm_full_frame (the
+ *                      paper's first frame: the whole range, Section 2.4)
+ * roles: host array of B bytes.  left, right: B*H*W uint8 each (device or
+ * host); every slot's images are read, but only those of advancing slots
+ * matter.  R, t, K, baseline as in rsgm_reduced_frame (R and t of idle and
+ * full slots are ignored).  A slot's results do not depend on the roles of
+ * the others.  A reduced slot without a state: RSGM_ERR_NO_STATE; a role
+ * other than the three: RSGM_ERR_INVALID_ARG.  All slots idle: nothing is
+ * enqueued.
+ */
+#define RSGM_SLOT_IDLE 0
+#define RSGM_SLOT_REDUCED 1
+#define RSGM_SLOT_FULL 2
+int rsgm_slot_frame(rsgm_stream s, const uint8_t *roles, const uint8_t *left, const uint8_t *right,
+                    const float *R, const float *t, const float *K, float baseline);
 
 /*
  * Copies the current state out: disparity d (float), variance p (float),
@@ -158,7 +182,8 @@ int rsgm_set_state(rsgm_stream s, const float *disp, const float *var);
 #define RSGM_BUF_WINDOW 2     /* uint32 per pixel: lo | (width << 16) */
 #define RSGM_BUF_OFFSET 3     /* uint32 per pixel: first cell of the pixel's window in the
                                  RSGM_BUF_COST / _AGGREGATED layout (prefix sum of the widths) */
-#define RSGM_BUF_CLASS 4      /* uint8 per pixel: 0 predicted, 1 discontinuity reset, 2 no prediction */
+#define RSGM_BUF_CLASS 4      /* uint8 per pixel: 0 predicted, 1 discontinuity reset, 2 no prediction,
+                                 3 idle slot (rsgm_slot_frame) */
 #define RSGM_BUF_D_PRED 5     /* float per pixel: predicted disparity (undefined where class 2) */
 #define RSGM_BUF_P_PRED 6     /* float per pixel: predicted variance (undefined where class 2) */
 #define RSGM_BUF_COST 7       /* uint8 per cell, N cells: ragged cost volume, pixels' windows
@@ -242,7 +267,7 @@ int rsgm_detect(rsgm_stream s, const rsgm_detect_params *p, rsgm_box *boxes, int
  * (so that areas and the exact IoU comparisons cannot overflow); otherwise
  * RSGM_ERR_INVALID_ARG.
  */
-#define RSGM_BOX_COORD_LIMIT (1 << 20)
+#define RSGM_BOX_COORD_LIMIT 1048576 /* 2^20 */
 int rsgm_group_boxes(const rsgm_box *in, int32_t n, int32_t iou_num, int32_t iou_den, int32_t min_area,
                      rsgm_box *out, int32_t capacity, int32_t *count);
 
@@ -357,9 +382,8 @@ int rsgm_group_destroy(rsgm_group g);
 #define RSGM_CNN_PARAMS 21414
 typedef struct rsgm_cnn_s *rsgm_cnn;
 
-/* Creates a network on the current device from host parameters, used and
- * trained on `cuda_stream` (may be NULL).  Every handle it is attached to
- * must use the same stream. */
+/* Creates a network on the current device from host parameters, trained on
+ * `cuda_stream` (may be NULL). */
 int rsgm_cnn_create(rsgm_cnn *out, const float *params, void *cuda_stream);
 
 /* Copies the current parameters, or the gradient of the latest training
@@ -371,16 +395,20 @@ int rsgm_cnn_grad(rsgm_cnn c, float *grad);
  * handle it is attached to.  NULL is a no-op. */
 int rsgm_cnn_destroy(rsgm_cnn c);
 
-/* Attaches the network to a handle created with RSGM_RADIUS_LEARNED (same
- * device and CUDA stream).  Allocates the handle's per-pixel network buffers:
- * 261 bytes per pixel, plus 160 at the first training step.  Its reduced
- * frames then run the network after the prediction.  A learned handle
- * cannot join a group. */
+/* Attaches the network to a handle created with RSGM_RADIUS_LEARNED on the
+ * same device.  Allocates the handle's per-pixel network buffers: 261 bytes
+ * per pixel, plus 160 at the first training step.  Its reduced frames then
+ * run the network after the prediction.  Frames only read the network, so
+ * handles on different CUDA streams may share one network (a request loop
+ * serving many streams); a training step changes it, on the network's own
+ * stream, so frames of handles on other streams must not overlap a training
+ * step.  A learned handle cannot join a group. */
 int rsgm_attach_cnn(rsgm_stream s, rsgm_cnn c);
 
 /*
  * One training step on the handle's latest reduced frame, against a target
- * disparity map (device, B*H*W floats).  The step reruns the network on the
+ * disparity map (device, B*H*W floats).  The handle must use the network's
+ * CUDA stream (RSGM_ERR_INVALID_ARG otherwise).  The step reruns the network on the
  * frame's stored inputs with the current parameters, so repeated steps on
  * one frame descend properly.  The target is typically the state
  * of a full-range (RSGM_RADIUS_FULL) handle on the same frames.

@@ -51,6 +51,10 @@ RSGM_PEAK_U16X2_MIN = 2
 RSGM_PEAK_U16X2_MIX = 3
 PEAK_NAMES = ("i32_add", "i32_min", "u16x2_min", "u16x2_mix")
 
+RSGM_SLOT_IDLE = 0
+RSGM_SLOT_REDUCED = 1
+RSGM_SLOT_FULL = 2
+
 RSGM_STAGE_PREDICT = 0
 RSGM_STAGE_SCAN = 1
 RSGM_STAGE_CENSUS = 2
@@ -72,6 +76,7 @@ class rsgm_params(ctypes.Structure):
 
 
 RSGM_MAX_WINDOW_SIZES = 8
+RSGM_BOX_COORD_LIMIT = 1 << 20
 
 
 class rsgm_box(ctypes.Structure):
@@ -101,6 +106,7 @@ SIGNATURES = {
     "rsgm_footprint": (ctypes.c_int, [ctypes.POINTER(rsgm_params), ctypes.POINTER(ctypes.c_uint64)]),
     "rsgm_full_frame": (ctypes.c_int, [_P, _P, _P]),
     "rsgm_reduced_frame": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_float]),
+    "rsgm_slot_frame": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float]),
     "rsgm_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "rsgm_set_state": (ctypes.c_int, [_P, _P, _P]),
     "rsgm_read_buffer": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -237,6 +243,20 @@ def rsgm_reduced_frame(h: int, left, right, R, t, K, baseline: float):
     Ka = _host_f32(K, 9)
     _check(lib().rsgm_reduced_frame(h, _ptr(left), _ptr(right), _ptr(Ra), _ptr(ta), _ptr(Ka),
                                     float(baseline)), "rsgm_reduced_frame")
+
+
+def rsgm_slot_frame(h: int, roles, left, right, R, t, K, baseline: float):
+    """roles: B values of RSGM_SLOT_IDLE / _REDUCED / _FULL; R: B x 3 x 3,
+    t: B x 3, K: 3 x 3 (host arrays or CPU tensors)."""
+    import numpy as np
+    ro = np.ascontiguousarray(np.asarray(roles, np.uint8).reshape(-1))
+    Ra = _host_f32(R)
+    if Ra.size != 9 * ro.size:
+        raise ValueError("R must hold one 3x3 matrix per slot")
+    ta = _host_f32(t, 3 * ro.size)
+    Ka = _host_f32(K, 9)
+    _check(lib().rsgm_slot_frame(h, _ptr(ro), _ptr(left), _ptr(right), _ptr(Ra), _ptr(ta), _ptr(Ka),
+                                 float(baseline)), "rsgm_slot_frame")
 
 
 def rsgm_state(h: int, disp=None, var=None, moving_mask=None, disp_int=None):

@@ -6,12 +6,12 @@
 // of a path.  Each enabled direction writes its own plane of L_r; the update
 // kernel sums the planes into S.
 //
-// One lane walks one path line; a warp walks 32 adjacent parallel lines in
-// lockstep, so for vertical and diagonal directions its lanes visit 32
-// consecutive pixels of one image row at every step (coalesced metadata,
-// cost and plane accesses).  Losses are held as two 16-bit values per 32-bit
+// One lane walks one path line; a warp walks 32 parallel lines in lockstep
+// (for vertical and diagonal directions, 8 groups of 4 adjacent lines, whose
+// lanes visit 4 consecutive pixels of one image row at every step).  Losses are held as two 16-bit values per 32-bit
 // register and combined with packed minima and carry-free 32-bit additions.
 #include "rsgm_internal.cuh"
+#include <stdlib.h>
 
 namespace rsgm {
 namespace {
@@ -23,7 +23,6 @@ constexpr unsigned kFull = 0xffffffffu;
 // m + P2, and inf + P1 still fits 16 bits: no operation carries or borrows
 // across the two halves.
 constexpr unsigned kInf2 = 0x40004000u;
-constexpr int kWideIters = (RSGM_MAX_DISP + 127) / 128;  // 4 cells per lane per pass over a wide window
 
 __device__ __forceinline__ unsigned vmin2(unsigned a, unsigned b)
 {
@@ -89,8 +88,11 @@ __device__ __forceinline__ void band_load(const unsigned *band, int t, int pad, 
 // slots [0, w) with +inf on [-pad, 0) and on [round4(w), round4(w) + pad);
 // reads that can see no slot of [0, w) take +inf without loading.
 //
-// Metadata is fetched two steps ahead and narrow costs one step ahead.
-template <typename T, int NR, bool kCheap>
+// Metadata is fetched two steps ahead; narrow costs, and the costs of the
+// first two wide pixels of a step, one step ahead.  Wide pixels go two at a
+// time, one per half-warp, 8 cells per lane: KW passes of 128 cells cover a
+// window.
+template <typename T, int NR, int KW, bool kCheap>
 __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok, const uint8_t *__restrict__ cost,
                                      T *__restrict__ plane, const uint2 *__restrict__ meta, const LinePlan &plan,
                                      unsigned *band_all, unsigned *band)
@@ -136,24 +138,47 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
     int plo = 0, pw = 0, pm = 0;  // predecessor window and minimum; pw = 0: no predecessor
     bool inband = false;          // the predecessor's losses are in the band, not in P
 
-    uint2 mc = meta_at(s0), mn = meta_at(s0 + 1);
-    unsigned cc[NW];
-    {
-        const int w = (int)(mc.y >> 16);
-        const unsigned *src = (const unsigned *)(cost + mc.x);
+    // This lane's cost words of the first pass over the wide windows among
+    // the pixels of `m`: the first two wide pixels, one per half-warp, 8
+    // cells per lane and 128-cell pass.
+    auto fetch_wide = [&](const uint2 &m, unsigned (&wp)[KW][2]) {
+        unsigned wm = __ballot_sync(kFull, (int)(m.y >> 16) > NC);
 #pragma unroll
-        for (int q = 0; q < NW; ++q) cc[q] = (w > 0 && w <= NC) ? src[q] : 0u;
-    }
+        for (int it = 0; it < KW; ++it) wp[it][0] = wp[it][1] = 0u;
+        if (!wm) return;  // uniform: no wide pixel among them
+        const int sa = __ffs(wm) - 1;
+        wm &= wm - 1;
+        const int sb = wm ? __ffs(wm) - 1 : sa;
+        const int src = (lane >> 4) ? sb : sa;
+        const unsigned so = __shfl_sync(kFull, m.x, src), sw = __shfl_sync(kFull, m.y >> 16, src);
+        const bool mine = !(lane >> 4) || sb != sa;
+#pragma unroll
+        for (int it = 0; it < KW; ++it) {
+            const unsigned c0 = 8u * (lane & 15) + 128u * it;
+            if (mine && c0 < sw) {
+                const unsigned *p = (const unsigned *)(cost + so + c0);
+                wp[it][0] = p[0];
+                wp[it][1] = p[1];
+            }
+        }
+    };
+    auto fetch_narrow = [&](const uint2 &m, unsigned (&c)[NW]) {
+        const int w = (int)(m.y >> 16);
+        const unsigned *src = (const unsigned *)(cost + m.x);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) c[q] = (w > 0 && w <= NC) ? src[q] : 0u;
+    };
+
+    uint2 mc = meta_at(s0), mn = meta_at(s0 + 1);
+    unsigned cc[NW], wc[KW][2];
+    fetch_narrow(mc, cc);
+    fetch_wide(mc, wc);
 #pragma unroll 2
     for (int s = s0; s <= s1; ++s) {
         const uint2 mnn = meta_at(s + 2);
-        unsigned cn[NW];
-        {
-            const int w = (int)(mn.y >> 16);
-            const unsigned *src = (const unsigned *)(cost + mn.x);
-#pragma unroll
-            for (int q = 0; q < NW; ++q) cn[q] = (w > 0 && w <= NC) ? src[q] : 0u;
-        }
+        unsigned cn[NW], wn[KW][2];
+        fetch_narrow(mn, cn);
+        fetch_wide(mn, wn);
         const unsigned o = mc.x;
         const int lo = (int)(mc.y & 0xFFFFu), w = (int)(mc.y >> 16);
 
@@ -226,7 +251,7 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
             inband = false;
         }
 
-        // ---- wide: the whole warp, one pixel at a time
+        // ---- wide: the whole warp, two pixels at a time (one per half-warp)
         unsigned wide = __ballot_sync(kFull, w > NC);
         if (wide) {
             if (w > NC && pw > 0 && !inband) {
@@ -235,69 +260,102 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
                 for (int q = 0; q < (pad >> 1); ++q) band[(pad >> 1) + NR + q] = kInf2;
             }
             __syncwarp();
-            while (wide) {
-                const int src = __ffs(wide) - 1;
+            const int half = lane >> 4, hl = lane & 15;
+            for (int jp = 0; wide; ++jp) {
+                const int sa = __ffs(wide) - 1;
                 wide &= wide - 1;
+                const int sb = wide ? __ffs(wide) - 1 : sa;
+                if (sb != sa) wide &= wide - 1;
+                const int src = half ? sb : sa;
+                const bool mine = !half || sb != sa;  // this half-warp has a pixel
                 const unsigned so = __shfl_sync(kFull, o, src);
                 const unsigned f1 = __shfl_sync(kFull, (unsigned)lo | ((unsigned)w << 16), src);
                 const unsigned f2 = __shfl_sync(kFull, (unsigned)plo | ((unsigned)pw << 16), src);
                 const int spm = __shfl_sync(kFull, pm, src);
-                const int slo = (int)(f1 & 0xFFFFu), sw = (int)(f1 >> 16);
+                const int slo = (int)(f1 & 0xFFFFu), sw = mine ? (int)(f1 >> 16) : 0;
                 const int splo = (int)(f2 & 0xFFFFu), spw = (int)(f2 >> 16);
-                unsigned *sb = band_all + src * plan.band_words;
+                unsigned *sbd = band_all + src * plan.band_words;
                 const unsigned cap2 = spw ? (unsigned)(spm + plan.P2) * 0x10001u : 0u;
                 const unsigned m2 = spw ? (unsigned)spm * 0x10001u : 0u;
                 const unsigned w2 = (unsigned)sw * 0x10001u;
-                unsigned Lr[kWideIters][2];
+                unsigned Lr[KW][4];
                 unsigned run = kInf2;
 #pragma unroll
-                for (int it = 0; it < kWideIters; ++it) {
-                    const int c0 = 4 * lane + 128 * it;
-                    Lr[it][0] = Lr[it][1] = kInf2;
+                for (int it = 0; it < KW; ++it) {
+                    const int c0 = 8 * hl + 128 * it;
+                    Lr[it][0] = Lr[it][1] = Lr[it][2] = Lr[it][3] = kInf2;
                     if (c0 < sw) {
-                        unsigned U[3];
+                        unsigned U[5];
                         const int t0 = slo + c0 - 1 - splo;  // predecessor slot of d - 1 for cell c0
-                        if (spw == 0 || t0 >= spw || t0 + 5 < 0) {
-                            U[0] = U[1] = U[2] = kInf2;
+                        if (spw == 0 || t0 >= spw || t0 + 9 < 0) {
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) U[i] = kInf2;
                         } else {
-                            band_load<3>(sb, t0, pad, U);
+                            band_load<5>(sbd, t0, pad, U);
                         }
-                        const unsigned cw = *(const unsigned *)(cost + so + c0);
-                        unsigned c01 = __byte_perm(cw, 0u, 0x4140u), c23 = __byte_perm(cw, 0u, 0x4342u);
+                        unsigned cw0, cw1;  // the first pass's costs were fetched a step ahead
+                        if (jp == 0) {
+                            cw0 = wc[it][0];
+                            cw1 = wc[it][1];
+                        } else {
+                            const unsigned *p = (const unsigned *)(cost + so + c0);
+                            cw0 = p[0];
+                            cw1 = p[1];
+                        }
+                        // the second word lies past the window's run when c0 + 4 >= w: it
+                        // holds the next pixel's costs, which must not enter the minimum
+                        if (kCheap && c0 + 4 >= sw) cw1 = 0xFFFFFFFFu;
+                        unsigned c[4] = {__byte_perm(cw0, 0u, 0x4140u), __byte_perm(cw0, 0u, 0x4342u),
+                                         __byte_perm(cw1, 0u, 0x4140u), __byte_perm(cw1, 0u, 0x4342u)};
                         if (!kCheap) {
-                            c01 = mask_pair(c01, (unsigned)c0 | ((unsigned)(c0 + 1) << 16), w2);
-                            c23 = mask_pair(c23, (unsigned)(c0 + 2) | ((unsigned)(c0 + 3) << 16), w2);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                c[i] = mask_pair(c[i], (unsigned)(c0 + 2 * i) | ((unsigned)(c0 + 2 * i + 1) << 16), w2);
                         }
-                        const unsigned L0 = eq1(U[0], U[1], c01, P1x2, cap2, m2);
-                        const unsigned L1 = eq1(U[1], U[2], c23, P1x2, cap2, m2);
-                        run = vmin2(run, vmin2(L0, L1));
-                        if (sizeof(T) == 1)
-                            *(unsigned *)(plane + so + c0) = pack4(L0, L1);
-                        else
-                            *(uint2 *)(plane + so + c0) = make_uint2(L0, L1);
-                        Lr[it][0] = L0;
-                        Lr[it][1] = L1;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            Lr[it][i] = eq1(U[i], U[i + 1], c[i], P1x2, cap2, m2);
+                            run = vmin2(run, Lr[it][i]);
+                        }
+                        if (sizeof(T) == 1) {
+                            unsigned *dst = (unsigned *)(plane + so + c0);
+                            dst[0] = pack4(Lr[it][0], Lr[it][1]);
+                            if (c0 + 4 < sw) dst[1] = pack4(Lr[it][2], Lr[it][3]);
+                        } else {
+                            uint2 *dst = (uint2 *)(plane + so + c0);
+                            dst[0] = make_uint2(Lr[it][0], Lr[it][1]);
+                            if (c0 + 4 < sw) dst[1] = make_uint2(Lr[it][2], Lr[it][3]);
+                        }
                     }
                 }
-                const unsigned r = __reduce_min_sync(kFull, min(run & 0xFFFFu, run >> 16));
-                __syncwarp();  // every read of the source band is done
+                // minimum over each half-warp's cells
+                unsigned r = min(run & 0xFFFFu, run >> 16);
 #pragma unroll
-                for (int it = 0; it < kWideIters; ++it) {
-                    const int c0 = 4 * lane + 128 * it;
+                for (int off = 8; off >= 1; off >>= 1) r = min(r, __shfl_xor_sync(kFull, r, off));
+                const unsigned ra = __shfl_sync(kFull, r, 0), rb = __shfl_sync(kFull, r, 16);
+                __syncwarp();  // every read of the source bands is done
+#pragma unroll
+                for (int it = 0; it < KW; ++it) {
+                    const int c0 = 8 * hl + 128 * it;
                     if (c0 < sw) {
-                        // two 32-bit stores: bands have an odd word stride, so
-                        // a band word is not 8-byte aligned in general
-                        sb[((c0 + pad) >> 1)] = Lr[it][0];
-                        sb[((c0 + pad) >> 1) + 1] = Lr[it][1];
+                        // 32-bit stores: bands have an odd word stride, so a
+                        // band word is not 8-byte aligned in general
+                        unsigned *q = sbd + ((c0 + pad) >> 1);
+                        q[0] = Lr[it][0];
+                        q[1] = Lr[it][1];
+                        if (c0 + 4 < sw) {
+                            q[2] = Lr[it][2];
+                            q[3] = Lr[it][3];
+                        }
                     }
                 }
                 const int ext = (sw + 3) & ~3;
-                if (lane < (pad >> 1)) sb[((ext + pad) >> 1) + lane] = kInf2;
+                if (mine && hl < (pad >> 1)) sbd[((ext + pad) >> 1) + hl] = kInf2;
                 __syncwarp();
-                if (lane == src) {
-                    plo = slo;
-                    pw = sw;
-                    pm = (int)r;
+                if (lane == sa || lane == sb) {  // the sources take their own window
+                    plo = lo;
+                    pw = w;
+                    pm = (int)(lane == sa ? ra : rb);
                     inband = true;
                 }
             }
@@ -308,6 +366,11 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
         mn = mnn;
 #pragma unroll
         for (int q = 0; q < NW; ++q) cc[q] = cn[q];
+#pragma unroll
+        for (int it = 0; it < KW; ++it) {
+            wc[it][0] = wn[it][0];
+            wc[it][1] = wn[it][1];
+        }
     }
 }
 
@@ -315,8 +378,8 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
 __constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 __constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
-template <typename T, int NR, bool kCheap>
-__global__ void __launch_bounds__(kLineWarps * 32)
+template <typename T, int NR, int KW, bool kCheap>
+__global__ void __launch_bounds__(kLineWarps * 32, 5)
     k_lines(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
             const __grid_constant__ LinePlan plan)
 {
@@ -329,20 +392,29 @@ __global__ void __launch_bounds__(kLineWarps * 32)
     const int dir = plan.dir[si];
     const int dx = kDX[dir], dy = kDY[dir];
     const int nl = lines_per_stream(dx, dy, plan.g.W, plan.g.H);
-    const int wps = (nl + 31) / 32;
+    const int lpw = dy == 0 ? plan.hlines : 32;  // lines per warp
+    const int wps = (nl + lpw - 1) / lpw;
     const long long wi = gw - plan.warp_begin[si];
     const int b = (int)(wi / wps), kw = (int)(wi - (long long)b * wps);
     const int kbase = (dx > 0 && dy != 0) ? -(plan.g.H - 1) : 0;
-    const bool line_ok = kw * 32 + lane < nl;
+    // Lines are dealt to warps interleaved, so that every warp gets its share
+    // of the image's full-range regions (the borders without a prediction,
+    // rows of resets along depth edges): horizontal lines (rows, which no
+    // warp reads coalesced) one by one, vertical and diagonal lines in groups
+    // of 4 adjacent lines (32 bytes of metadata per group and step).  A
+    // horizontal line is W steps long, the longest chain of the launch, so
+    // horizontal warps may walk fewer than 32 rows to shorten their steps.
+    const int li = dy == 0 ? kw + lane * wps : ((kw + (lane >> 2) * wps) << 2) + (lane & 3);
+    const bool line_ok = li < nl && lane < lpw;
     unsigned *band_all = smem + warp * 32 * plan.band_words;
     unsigned *band = band_all + lane * plan.band_words;
     for (int q = 0; q < (plan.pad >> 1); ++q) band[q] = kInf2;  // slots [-pad, 0): always +inf
     __syncwarp();
     T *plane = planes + (long long)plan.plane_of[si] * plan.plane_stride;
-    walk<T, NR, kCheap>(dx, dy, b, kbase + kw * 32 + lane, line_ok, cost, plane, meta, plan, band_all, band);
+    walk<T, NR, KW, kCheap>(dx, dy, b, kbase + li, line_ok, cost, plane, meta, plan, band_all, band);
 }
 
-template <typename T, int NR, bool kCheap>
+template <typename T, int NR, int KW, bool kCheap>
 cudaError_t launch_nr(const Buffers &b, const LinePlan &plan, cudaStream_t st)
 {
     const long long warps = plan.warp_begin[plan.ndir];
@@ -351,22 +423,29 @@ cudaError_t launch_nr(const Buffers &b, const LinePlan &plan, cudaStream_t st)
     const size_t smem = (size_t)kLineWarps * 32 * plan.band_words * sizeof(unsigned);
     if (smem > 48 * 1024) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_lines<T, NR, kCheap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_lines<T, NR, KW, kCheap>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_lines<T, NR, kCheap><<<blocks, kLineWarps * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
+    k_lines<T, NR, KW, kCheap><<<blocks, kLineWarps * 32, smem, st>>>(b.cost, (T *)b.planes, b.meta, plan);
     return cudaGetLastError();
+}
+
+template <typename T, int KW, bool kCheap>
+cudaError_t launch_kw(const Buffers &b, const LinePlan &plan, int nr, cudaStream_t st)
+{
+    switch (nr) {
+    case 1: return launch_nr<T, 1, KW, kCheap>(b, plan, st);
+    case 3: return launch_nr<T, 3, KW, kCheap>(b, plan, st);
+    case 5: return launch_nr<T, 5, KW, kCheap>(b, plan, st);
+    default: return launch_nr<T, 9, KW, kCheap>(b, plan, st);
+    }
 }
 
 template <typename T, bool kCheap>
 cudaError_t launch_t(const Buffers &b, const LinePlan &plan, int nr, cudaStream_t st)
 {
-    switch (nr) {
-    case 1: return launch_nr<T, 1, kCheap>(b, plan, st);
-    case 3: return launch_nr<T, 3, kCheap>(b, plan, st);
-    case 5: return launch_nr<T, 5, kCheap>(b, plan, st);
-    default: return launch_nr<T, 9, kCheap>(b, plan, st);
-    }
+    // one pass of 128 cells covers every window up to D = 128
+    return plan.g.D <= 128 ? launch_kw<T, 1, kCheap>(b, plan, nr, st) : launch_kw<T, 2, kCheap>(b, plan, nr, st);
 }
 
 }  // namespace
@@ -390,8 +469,9 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     plan.plane_stride = plane_stride(g);
     const int nr = sweep_capacity(capacity) / 2;
     // +inf padding around a band's window: at least the widest read past it
-    // (a narrow read spans 2 NR + 2 slots), even so that slot 0 is word aligned
-    const int pad = max(6, 2 * nr + 2);
+    // (a narrow read spans 2 NR + 2 slots, a wide one 10), even so that slot 0
+    // is word aligned, and at most 32 words (one store per lane)
+    const int pad = max(10, 2 * nr + 2);
     plan.pad = (pad + 1) & ~1;
     // slots [-pad, round4(max(D, 2 NR)) + pad) in 32-bit words, an odd count
     // so that the lanes' bands fall in different shared-memory banks
@@ -399,6 +479,8 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     int words = (cap + 2 * plan.pad) / 2;
     if (!(words & 1)) ++words;
     plan.band_words = words;
+    plan.hlines = 16;
+    if (const char *e = getenv("RSGM_PROBE_HLINES")) plan.hlines = atoi(e);  // PROBE ONLY, not committed
     // Long lines first so that the tail of the launch is short: horizontal,
     // diagonal, vertical.  Planes are numbered by direction bit order.
     static const int order[8] = {0, 1, 4, 5, 6, 7, 2, 3};
@@ -409,7 +491,9 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     for (int kk = 0; kk < 8; ++kk) {
         const int dir = order[kk];
         if (!(path_mask & (1u << dir))) continue;
-        const long long warps = (long long)g.B * ((lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H) + 31) / 32);
+        const int lpw = kHostDY[dir] == 0 ? plan.hlines : 32;
+        const long long warps =
+            (long long)g.B * ((lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H) + lpw - 1) / lpw);
         plan.dir[plan.ndir] = dir;
         plan.plane_of[plan.ndir] = plane_index[dir];
         plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + warps;

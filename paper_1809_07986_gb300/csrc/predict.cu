@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) k_splat(const float *__restrict__ d,
     int b = (int)(gi / a.g.HW);
     int s = (int)(gi - (long long)b * a.g.HW);
     int y = s / a.g.W, x = s - y * a.g.W;
+    if (a.role[b] != RSGM_SLOT_REDUCED) return;  // idle streams and new streams predict nothing
     float ds = d[gi];
     if (!(ds > 0.5f)) return;
     const Motion &m = a.m[b];
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
     __shared__ unsigned total;
     const int row = blockIdx.x;  // b * H + y
     const int y = row % g.H;
+    const uint8_t role = fp.role[row / g.H];
     const long long rbase = (long long)row * g.W;
     unsigned carry = 0, cells = 0;
     for (int x0 = 0; x0 < g.W; x0 += kWinTile) {
@@ -205,7 +207,13 @@ __global__ void __launch_bounds__(256) k_window(const float *__restrict__ d_pred
             const float dc = sd[1][i + 1];
             int lo = 0, w = g.D;
             uint8_t c = 2;
-            if (dc >= 0.0f) {
+            if (role == RSGM_SLOT_IDLE) {
+                // an idle stream searches nothing and keeps its state
+                w = 0;
+                c = 3;
+            } else if (role == RSGM_SLOT_FULL) {
+                // a new stream's first frame: the whole range, no prediction
+            } else if (dc >= 0.0f) {
                 const float nb[4] = {sd[1][i], sd[1][i + 2], sd[0][i + 1], sd[2][i + 1]};
                 bool reset = false;
 #pragma unroll
@@ -341,9 +349,9 @@ cudaError_t launch_full_window(const Buffers &b, const Geometry &g, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, cudaStream_t st)
+cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, int nstreams, cudaStream_t st)
 {
-    k_row_scan<<<1, 256, 0, st>>>(b.row_total, b.row_cells, b.row_base, g.B * g.H, g.B, b.counters);
+    k_row_scan<<<1, 256, 0, st>>>(b.row_total, b.row_cells, b.row_base, g.B * g.H, nstreams, b.counters);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,8 @@ struct rsgm_stream_s {
     bool capturing;   // enqueueing into a group's graph: no stage-timing events
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
-    bool has_state;
+    bool has_state;                    // some stream of the handle has a state
+    uint8_t slot_state[RSGM_MAX_BATCH];  // per stream: 1 once it has a state
     Buffers buf;
     rsgm_cnn cnn;         // attached network (RSGM_RADIUS_LEARNED), not owned
     LearnedBuffers lb;    // its per-pixel buffers, owned
@@ -177,9 +178,10 @@ void free_cnn(rsgm_cnn c)
     }
 }
 
-FrameParams frame_params(const rsgm_stream_s *s)
+FrameParams frame_params(const rsgm_stream_s *s, const uint8_t *roles = nullptr, uint8_t all = RSGM_SLOT_REDUCED)
 {
     FrameParams fp;
+    for (int b = 0; b < RSGM_MAX_BATCH; ++b) fp.role[b] = b < s->g.B ? (roles ? roles[b] : all) : RSGM_SLOT_IDLE;
     fp.radius_mode = s->P.radius_mode;
     fp.radius = s->P.radius;
     fp.P1 = s->P.P1;
@@ -231,12 +233,14 @@ int mark(rsgm_stream s, int k)
 // Census, cost, aggregation and the update: the part shared by both frame
 // kinds.  A learned frame has run the census already (the network reads it)
 // and corrects with its per-pixel measurement variance r_map.
-int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool census_done, const float *r_map)
+int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool census_done, const float *r_map,
+                     const FrameParams &fp)
 {
     const Geometry &g = s->g;
-    FrameParams fp = frame_params(s);
+    int active = 0;
+    for (int b = 0; b < g.B; ++b) active += fp.role[b] != RSGM_SLOT_IDLE;
     RSGM_MARK(s, 1);
-    RSGM_CUDA(launch_row_scan(s->buf, g, s->st));
+    RSGM_CUDA(launch_row_scan(s->buf, g, active, s->st));
     RSGM_MARK(s, 2);
     if (!census_done) RSGM_CUDA(launch_census(s->buf, g, dl, dr, s->P.census_w, s->P.census_h, s->st));
     RSGM_MARK(s, 3);
@@ -258,7 +262,8 @@ int check_reduced_args(rsgm_stream s, const uint8_t *left, const uint8_t *right,
     if (!(baseline > 0.0f) || !(K[0] > 0.0f) || !(K[4] > 0.0f) || K[1] != 0.0f || K[3] != 0.0f ||
         K[6] != 0.0f || K[7] != 0.0f || K[8] != 1.0f)
         return fail(RSGM_ERR_INVALID_ARG, "K must be [fx 0 cx; 0 fy cy; 0 0 1] with fx, fy > 0; baseline > 0");
-    if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "reduced frame before any full frame or set_state");
+    for (int b = 0; b < s->g.B; ++b)
+        if (!s->slot_state[b]) return fail(RSGM_ERR_NO_STATE, "reduced frame of stream %d before its first frame", b);
     if (s->P.radius_mode == RSGM_RADIUS_LEARNED && !s->cnn)
         return fail(RSGM_ERR_INVALID_ARG, "RSGM_RADIUS_LEARNED handle without an attached network");
     return RSGM_OK;
@@ -267,7 +272,7 @@ int check_reduced_args(rsgm_stream s, const uint8_t *left, const uint8_t *right,
 // Enqueues one reduced frame of all the handle's streams on s->st (arguments
 // already checked, the handle's device current).
 int enqueue_reduced(rsgm_stream s, const uint8_t *left, const uint8_t *right, const float *R, const float *t,
-                    const float *K, float baseline)
+                    const float *K, float baseline, const uint8_t *roles = nullptr)
 {
     const uint8_t *dl, *dr;
     int rc = stage_images(s, left, right, &dl, &dr);
@@ -285,6 +290,7 @@ int enqueue_reduced(rsgm_stream s, const uint8_t *left, const uint8_t *right, co
     for (int b = 0; b < s->g.B; ++b) {
         memcpy(a->m[b].R, R + 9 * b, 9 * sizeof(float));
         memcpy(a->m[b].t, t + 3 * b, 3 * sizeof(float));
+        a->role[b] = roles ? roles[b] : (uint8_t)RSGM_SLOT_REDUCED;
     }
     rc = mark(s, 0);
     if (rc) {
@@ -301,9 +307,9 @@ int enqueue_reduced(rsgm_stream s, const uint8_t *left, const uint8_t *right, co
         RSGM_CUDA(launch_census(s->buf, s->g, dl, dr, s->P.census_w, s->P.census_h, s->st));
         RSGM_CUDA(cnn_forward(s->cnn->w, s->lb, s->buf, s->g, dl, s->nbits, s->st));
     }
-    FrameParams fp = frame_params(s);
+    FrameParams fp = frame_params(s, roles);
     RSGM_CUDA(launch_window(s->buf, s->g, fp, s->st));
-    rc = match_and_update(s, dl, dr, learned, learned ? s->lb.r_map : nullptr);
+    rc = match_and_update(s, dl, dr, learned, learned ? s->lb.r_map : nullptr, fp);
     if (rc) return rc;
     s->learned_frame = learned;
     return RSGM_OK;
@@ -457,6 +463,7 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
                   : (p->max_disp <= 18 ? p->max_disp : 2);
     s->p_reset = p->p_reset > 0.0f ? p->p_reset : (float)p->max_disp * (float)p->max_disp / 12.0f;
     s->has_state = false;
+    memset(s->slot_state, 0, sizeof(s->slot_state));
     memset(&s->buf, 0, sizeof(s->buf));
     Buffers &b = s->buf;
     const size_t n = (size_t)s->g.NPIX, rows = (size_t)p->batch * p->height;
@@ -506,9 +513,10 @@ int rsgm_full_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right)
     if (rc) return rc;
     RSGM_MARK(s, 0);
     RSGM_CUDA(launch_full_window(s->buf, s->g, s->st));
-    rc = match_and_update(s, dl, dr, false, nullptr);
+    rc = match_and_update(s, dl, dr, false, nullptr, frame_params(s, nullptr, RSGM_SLOT_FULL));
     if (rc) return rc;
     s->has_state = true;
+    memset(s->slot_state, 1, sizeof(s->slot_state));
     s->learned_frame = false;
     return RSGM_OK;
 }
@@ -521,6 +529,35 @@ int rsgm_reduced_frame(rsgm_stream s, const uint8_t *left, const uint8_t *right,
     DeviceGuard dg(s->device);
     if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
     return enqueue_reduced(s, left, right, R, t, K, baseline);
+}
+
+int rsgm_slot_frame(rsgm_stream s, const uint8_t *roles, const uint8_t *left, const uint8_t *right, const float *R,
+                    const float *t, const float *K, float baseline)
+{
+    if (!s || !roles) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or roles");
+    int nact = 0;
+    for (int b = 0; b < s->g.B; ++b) {
+        if (roles[b] > RSGM_SLOT_FULL) return fail(RSGM_ERR_INVALID_ARG, "role %d of stream %d", roles[b], b);
+        nact += roles[b] != RSGM_SLOT_IDLE;
+    }
+    if (!left || !right || !R || !t || !K) return fail(RSGM_ERR_INVALID_ARG, "NULL image or motion array");
+    if (!(baseline > 0.0f) || !(K[0] > 0.0f) || !(K[4] > 0.0f) || K[1] != 0.0f || K[3] != 0.0f ||
+        K[6] != 0.0f || K[7] != 0.0f || K[8] != 1.0f)
+        return fail(RSGM_ERR_INVALID_ARG, "K must be [fx 0 cx; 0 fy cy; 0 0 1] with fx, fy > 0; baseline > 0");
+    for (int b = 0; b < s->g.B; ++b)
+        if (roles[b] == RSGM_SLOT_REDUCED && !s->slot_state[b])
+            return fail(RSGM_ERR_NO_STATE, "reduced frame of stream %d before its first frame", b);
+    if (s->P.radius_mode == RSGM_RADIUS_LEARNED && !s->cnn)
+        return fail(RSGM_ERR_INVALID_ARG, "RSGM_RADIUS_LEARNED handle without an attached network");
+    if (nact == 0) return RSGM_OK;  // nothing advances
+    DeviceGuard dg(s->device);
+    if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
+    int rc = enqueue_reduced(s, left, right, R, t, K, baseline, roles);
+    if (rc) return rc;
+    for (int b = 0; b < s->g.B; ++b)
+        if (roles[b] == RSGM_SLOT_FULL) s->slot_state[b] = 1;
+    s->has_state = true;
+    return RSGM_OK;
 }
 
 int rsgm_state(rsgm_stream s, float *disp, float *var, uint8_t *moving_mask, int16_t *disp_int)
@@ -547,6 +584,7 @@ int rsgm_set_state(rsgm_stream s, const float *disp, const float *var)
     RSGM_CUDA(cudaMemcpyAsync(s->buf.d, disp, n * sizeof(float), cudaMemcpyDefault, s->st));
     RSGM_CUDA(cudaMemcpyAsync(s->buf.p, var, n * sizeof(float), cudaMemcpyDefault, s->st));
     s->has_state = true;
+    memset(s->slot_state, 1, sizeof(s->slot_state));
     return RSGM_OK;
 }
 
@@ -884,8 +922,7 @@ int rsgm_attach_cnn(rsgm_stream s, rsgm_cnn c)
     if (!s || !c) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or network");
     if (s->P.radius_mode != RSGM_RADIUS_LEARNED)
         return fail(RSGM_ERR_INVALID_ARG, "the handle was not created with RSGM_RADIUS_LEARNED");
-    if (s->device != c->device || s->st != c->st)
-        return fail(RSGM_ERR_INVALID_ARG, "the network and the handle must share one device and one CUDA stream");
+    if (s->device != c->device) return fail(RSGM_ERR_INVALID_ARG, "the network and the handle must share one device");
     DeviceGuard dg(s->device);
     if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
     if (!s->lb.feats) {
@@ -916,6 +953,7 @@ int rsgm_cnn_train_step(rsgm_cnn c, rsgm_stream s, const float *d_target, float 
 {
     if (!c || !s || !d_target) return fail(RSGM_ERR_INVALID_ARG, "NULL network, handle or target");
     if (s->cnn != c) return fail(RSGM_ERR_INVALID_ARG, "the network is not attached to this handle");
+    if (s->st != c->st) return fail(RSGM_ERR_INVALID_ARG, "training runs on the network's own CUDA stream");
     if (!s->learned_frame) return fail(RSGM_ERR_NO_STATE, "no learned reduced frame to train on");
     if (!(lr >= 0.0f)) return fail(RSGM_ERR_INVALID_ARG, "lr must be >= 0");
     DeviceGuard dg(s->device);

@@ -33,11 +33,16 @@ struct Motion {
     float t[3];
 };
 
+// Role of each stream ("slot") of a handle in a frame: RSGM_SLOT_IDLE,
+// RSGM_SLOT_REDUCED or RSGM_SLOT_FULL (include/rsgm.h).
+typedef uint8_t SlotRoles[RSGM_MAX_BATCH];
+
 // Kernel argument block of the forward splat (passed by value; copied at launch).
 struct SplatArgs {
     Geometry g;
     float fx, fy, cx, cy, fb, q;
     Motion m[RSGM_MAX_BATCH];
+    SlotRoles role;  // only RSGM_SLOT_REDUCED streams are predicted
 };
 
 // Launch plan of the aggregation kernel: the enabled directions in launch
@@ -49,6 +54,7 @@ struct LinePlan {
     int P1, P2;
     int pad;         // +inf slots kept on both sides of a band's window
     int band_words;  // 32-bit words of shared memory per lane
+    int hlines;      // rows a warp walks for the horizontal directions (8, 16 or 32)
     int ndir;
     int dir[8];
     int plane_of[8];
@@ -68,11 +74,12 @@ struct DetectPlan {
     unsigned thresh_q;  // mean |nu| threshold in 1/16 px
 };
 
-// Per-frame scalar parameters of the resolve / update kernels.
+// Per-frame parameters of the resolve / update kernels.
 struct FrameParams {
     int radius_mode, radius;
     int P1, P2, nbits;
     float q, r_meas, p_reset, tau_disc, gamma;
+    SlotRoles role;
 };
 
 // Device buffers owned by a handle (all sized at the worst case at init).
@@ -83,7 +90,7 @@ struct Buffers {
     unsigned long long *key;            // splat z-buffer, NPIX, zero between frames
     float *d_pred, *p_pred;             // prediction after hole fill / reset, NPIX each
     uint32_t *win;                      // lo | width << 16, NPIX
-    uint8_t *cls;                       // 0 predicted, 1 reset, 2 no prediction
+    uint8_t *cls;                       // 0 predicted, 1 reset, 2 no prediction, 3 idle slot
     uint32_t *inrow;                    // exclusive offset within the pixel's row, NPIX
     uint2 *meta;                        // (first cell, window) of the pixel, NPIX
     uint32_t *row_total, *row_base;     // B*H each: rounded cells of the row, first cell of the row
@@ -160,7 +167,8 @@ cudaError_t launch_splat(const Buffers &b, const SplatArgs &a, cudaStream_t st);
 cudaError_t launch_gather_fill(const Buffers &b, const Geometry &g, float q, cudaStream_t st);
 cudaError_t launch_window(const Buffers &b, const Geometry &g, const FrameParams &fp, cudaStream_t st);
 cudaError_t launch_full_window(const Buffers &b, const Geometry &g, cudaStream_t st);
-cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, cudaStream_t st);
+// nstreams: the streams that advance this frame (counted as frames).
+cudaError_t launch_row_scan(const Buffers &b, const Geometry &g, int nstreams, cudaStream_t st);
 
 // Matching (Section 2.1).
 cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *left,

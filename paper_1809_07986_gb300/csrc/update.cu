@@ -13,7 +13,7 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b)
 
 constexpr int kUpdWarps = 4;
 constexpr int kStageCells = 1024;  // per-warp staging of S; larger spans read S from global memory
-constexpr int kLaneScan = 16;      // unstaged windows up to this width are scanned by their own lane
+constexpr int kLaneScan = 16;      // windows up to this width are scanned by their own lane
 constexpr unsigned kFull = 0xffffffffu;
 
 // S = sum of the direction planes over the cells [c0, c1), written to S and to
@@ -83,10 +83,10 @@ __device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, 
 // warp first sums the direction planes cell by cell with coalesced loads,
 // S(p,d) = sum_r L_r(p,d) (Section 2.2), writes S and, for spans of up to
 // kStageCells cells, stages it in shared memory.  d_int = first minimum of S
-// over the window: each lane scans its own pixel's window in the staged copy
-// or, when S stays in global memory, a window of up to kLaneScan cells; wider
-// unstaged windows are scanned by the whole warp with coalesced loads, one
-// pixel at a time, as a minimum of (S << 16 | k) keys.  With both neighbours inside the window and den = S- - 2 S0 + S+ > 0
+// over the window: each lane scans its own pixel's window of up to kLaneScan
+// cells; wider windows are scanned by the whole warp, one pixel at a time, as
+// a minimum of (S << 16 | k) keys, from the staged copy or with coalesced
+// loads.  With both neighbours inside the window and den = S- - 2 S0 + S+ > 0
 // the measurement is d_int + (S- - S+) / (2 den).  Pixels without a
 // prediction take the measurement (d = d_z, p = r).  Otherwise
 // nu = d_z - d_pred; if nu^2 > gamma (p_pred + r) the pixel is flagged and
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     const uint16_t *s = staged ? stage + (m.x - span0) : S + m.x;
     int best = 0;
     unsigned bs = 0;
-    if (valid && (staged || w <= kLaneScan)) {
+    if (valid && w > 0 && w <= kLaneScan) {
         bs = s[0];
         for (int k = 1; k < w; ++k) {
             const unsigned v = s[k];
@@ -133,14 +133,14 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
             }
         }
     }
-    if (!staged) {
+    {
         unsigned wide = __ballot_sync(kFull, valid && w > kLaneScan);
         while (wide) {
             const int src = __ffs(wide) - 1;
             wide &= wide - 1;
             const unsigned off = __shfl_sync(kFull, m.x, src);
             const int ww = __shfl_sync(kFull, w, src);
-            const uint16_t *s2 = S + off;
+            const uint16_t *s2 = staged ? stage + (off - span0) : S + off;
             unsigned key = 0xFFFFFFFFu;  // S in the high half, k in the low: the first minimum wins
             for (int k = lane; k < ww; k += 32) key = min(key, ((unsigned)s2[k] << 16) | (unsigned)k);
             key = __reduce_min_sync(kFull, key);
@@ -151,6 +151,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
         }
     }
     if (!valid) return;
+    const uint8_t role = fp.role[gi / g.HW];
+    if (role == RSGM_SLOT_IDLE) return;  // the stream sits this frame out: state and outputs unchanged
     int di = lo + best;
     float dz = (float)di;
     if (best >= 1 && best + 1 < w) {
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     }
     d_int[gi] = (int16_t)di;
     d_z[gi] = dz;
-    float r = r_map ? r_map[gi] : fp.r_meas;  // per pixel with the learned window
+    // per pixel with the learned window; a new stream's first frame uses r_meas
+    float r = (r_map && role != RSGM_SLOT_FULL) ? r_map[gi] : fp.r_meas;
     if (cls[gi] == 2) {
         d[gi] = dz;
         p[gi] = r;

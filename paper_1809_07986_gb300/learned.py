@@ -86,21 +86,33 @@ def bad_pixel_rate(d, gt) -> float:
     return float(((err > 3.0) & (err > 0.05 * gt) & ok).sum() / max(ok.sum(), 1))
 
 
-def evaluate(cnn, seeds, batch: int = 32, fixed_radius: int = 8, reps: int = 5, device="cuda"):
-    """Reduced frame 1 of the held-out pairs, learned window against the fixed
-    half-width: frames/s of the reduced frame (CUDA events, the full frame
-    excluded) and bad-pixel rates against the renderer's ground truth."""
+def bad_vs_full(d, d_full) -> float:
+    """Share of pixels whose disparity differs from the full-range result (the
+    plain method on the same frames) by more than 3 px."""
+    return float((np.abs(np.asarray(d, np.float64) - np.asarray(d_full, np.float64)) > 3.0).mean())
+
+
+def evaluate(cnn, seeds, batch: int = 32, fixed_radius: int = 4, reps: int = 5, device="cuda", untrained=None):
+    """Reduced frame 1 of the held-out pairs: the learned window against the
+    fixed half-width (config 1's +-4 by default) and, if `untrained` holds a
+    network, against that network.  Reports frames/s of the reduced frame
+    (CUDA events, the full frame excluded), cells searched, and bad-pixel
+    rates against the full-range result on the same frames (> 3 px) and
+    against the renderer's ground truth (> 3 px and > 5 %)."""
     import torch
     from . import Stream
     cs = torch.cuda.current_stream()
     seeds = list(seeds)[: (len(seeds) // batch) * batch]
-    out = {}
-    for name in ("learned", "fixed"):
-        mode = B.RSGM_RADIUS_LEARNED if name == "learned" else B.RSGM_RADIUS_FIXED
+    arms = [("full", B.RSGM_RADIUS_FULL, None), ("fixed", B.RSGM_RADIUS_FIXED, None),
+            ("learned", B.RSGM_RADIUS_LEARNED, cnn)]
+    if untrained is not None:
+        arms.append(("untrained", B.RSGM_RADIUS_LEARNED, untrained))
+    out, full_d = {}, {}
+    for name, mode, net in arms:
         st = Stream(B.rsgm_default_params(W, H, max_disp=D, batch=batch, radius_mode=mode, radius=fixed_radius), cs)
-        if name == "learned":
-            B.rsgm_attach_cnn(st.handle, cnn)
-        bad, ms, cells = [], 0.0, 0
+        if net is not None:
+            B.rsgm_attach_cnn(st.handle, net)
+        bad, badf, ms, cells = [], [], 0.0, 0
         try:
             for i in range(0, len(seeds), batch):
                 L, R, gt, Rm, tv, K, b = pairs(seeds[i:i + batch], device)
@@ -115,28 +127,38 @@ def evaluate(cnn, seeds, batch: int = 32, fixed_radius: int = 8, reps: int = 5, 
                     ms += e0.elapsed_time(e1)
                     cells += st.counters()[1] - c0
                 d = st.state()[0].cpu().numpy()
+                if name == "full":
+                    full_d[i] = d
                 bad.append(bad_pixel_rate(d, gt[1].cpu().numpy()))
+                badf.append(bad_vs_full(d, full_d[i]))
         finally:
             st.close()
         n = len(seeds) * reps
         out[name] = {"frames_per_s": n / (ms / 1e3), "cells_per_frame": cells / n,
-                     "bad_pixel_rate": float(np.mean(bad))}
+                     "bad_vs_full": float(np.mean(badf)), "bad_pixel_rate_gt": float(np.mean(bad))}
     out["speedup"] = out["learned"]["frames_per_s"] / out["fixed"]["frames_per_s"]
-    out["bad_pixel_delta_pp"] = 100.0 * (out["learned"]["bad_pixel_rate"] - out["fixed"]["bad_pixel_rate"])
+    out["bad_vs_full_delta_pp"] = 100.0 * (out["learned"]["bad_vs_full"] - out["fixed"]["bad_vs_full"])
+    out["bad_gt_delta_pp"] = 100.0 * (out["learned"]["bad_pixel_rate_gt"] - out["fixed"]["bad_pixel_rate_gt"])
     out["fixed_radius"] = fixed_radius
     return out
 
 
-def run(train_frames: int = 2000, eval_pairs: int = 64, batch: int = 32, lr: float = 3e-3, epochs: int = 1):
-    """Trains on train_frames / 2 pairs (two frames each) and evaluates on held-out pairs."""
+def run(train_frames: int = 2000, eval_pairs: int = 64, batch: int = 32, lr: float = 3e-3, epochs: int = 1,
+        fixed_radius: int = 4):
+    """Trains on train_frames / 2 pairs (two frames each) and evaluates on
+    held-out pairs against the fixed half-width and the untrained network."""
     t0 = time.perf_counter()
     seeds = list(range(10_000, 10_000 + train_frames // 2))
     cnn, theta, losses = train(seeds, batch=batch, lr=lr, epochs=epochs)
     t1 = time.perf_counter()
+    import torch
+    untrained = B.rsgm_cnn_create(init_params(0), torch.cuda.current_stream())
     try:
-        ev = evaluate(cnn, range(90_000, 90_000 + eval_pairs), batch=batch)
+        ev = evaluate(cnn, range(90_000, 90_000 + eval_pairs), batch=batch, fixed_radius=fixed_radius,
+                      untrained=untrained)
     finally:
         B.rsgm_cnn_destroy(cnn)
+        B.rsgm_cnn_destroy(untrained)
     ev.update(train_frames=2 * len(seeds) * epochs, train_s=t1 - t0, loss_first=losses[0] if losses else None,
               loss_last=losses[-1] if losses else None, steps=len(losses))
     return ev

@@ -90,6 +90,7 @@ def test_null_arguments(rs):
     assert L.rsgm_sync(None) == rs.RSGM_ERR_INVALID_ARG
     assert L.rsgm_destroy_stream(None) == rs.RSGM_OK
     assert L.rsgm_default_params(None, 1, 1) == rs.RSGM_ERR_INVALID_ARG
+    assert L.rsgm_slot_frame(None, None, None, None, None, None, None, 0.5) == rs.RSGM_ERR_INVALID_ARG
     v = ctypes.c_double()
     assert L.rsgm_measure_int_peak(7, None, ctypes.byref(v)) == rs.RSGM_ERR_INVALID_ARG
     assert L.rsgm_measure_int_peak(rs.RSGM_PEAK_I32_ADD, None, None) == rs.RSGM_ERR_INVALID_ARG

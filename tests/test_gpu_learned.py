@@ -210,6 +210,7 @@ def test_training_driver_runs_end_to_end(rs):
         ev = learned.evaluate(cnn, range(600, 604), batch=4, reps=1)
     finally:
         rs.rsgm_cnn_destroy(cnn)
-    for k in ("learned", "fixed"):
-        assert ev[k]["frames_per_s"] > 0 and 0.0 <= ev[k]["bad_pixel_rate"] <= 1.0
-        assert ev[k]["cells_per_frame"] > 0
+    for k in ("learned", "fixed", "full"):
+        assert ev[k]["frames_per_s"] > 0 and 0.0 <= ev[k]["bad_pixel_rate_gt"] <= 1.0
+        assert 0.0 <= ev[k]["bad_vs_full"] <= 1.0 and ev[k]["cells_per_frame"] > 0
+    assert ev["full"]["bad_vs_full"] == 0.0 and ev["fixed_radius"] == 4

@@ -1,9 +1,10 @@
 """The request loop on the GPU: streams of different resolutions arrive as
-Poisson processes and overlap on the device; every stream's final state is
-bit-identical to the same frames run alone on a fresh handle, and equal to
-the oracle's state chained over the stream's frames (integers bit-exact, the
-Kalman mean and variance within 1e-5 relative of the single-precision
-oracle)."""
+Poisson processes; streams of one geometry share launches of a pool handle
+(continuous batching) and pools overlap on the device.  Every stream's final
+state is bit-identical to the same frames run alone on a handle of its own,
+for the fixed and for the learned search window, and equal to the oracle's
+state chained over the stream's frames (integers bit-exact, the Kalman mean
+and variance within 1e-5 relative of the single-precision oracle)."""
 import numpy as np
 import pytest
 import torch
@@ -21,33 +22,55 @@ def rs():
     return rs
 
 
-def test_serving_results_equal_alone_results(rs):
+GEOMS = [(160, 120, 32, 100.0), (200, 100, 48, 150.0), (160, 120, 32, 100.0), (240, 96, 64, 200.0),
+         (200, 100, 48, 150.0), (160, 120, 32, 100.0)]
+
+
+def _mix(seed, geoms, frames=(4, 8), rates=(20, 60), spread=0.05):
     import synth
-    from paper_1809_07986_gb300.serving import GpuBackend, StreamSpec, poisson_arrivals, serve
-    rng = np.random.default_rng(5)
-    geoms = [(160, 120, 32, 100.0), (200, 100, 48, 150.0), (240, 96, 64, 200.0), (160, 120, 32, 100.0)]
-    specs, frames = [], {}
+    from paper_1809_07986_gb300.serving import StreamSpec, poisson_arrivals
+    rng = np.random.default_rng(seed)
+    specs, data = [], {}
     for i, (W, H, D, f) in enumerate(geoms):
-        n = 6
-        s = synth.kitti_like_sequence(700 + i, n_frames=n, width=W, height=H, f=f, baseline=0.54, device="cuda")
-        frames[i] = dict(left=s["left"], right=s["right"], R=s["R"], t=s["t"], K=s["K"], baseline=0.54)
-        specs.append(StreamSpec(i, W, H, D, 0.02 * i, poisson_arrivals(rng, 0.02 * i, 40.0, n)))
-    backend = GpuBackend(frames)
-    budget = sum(backend.footprint(s) for s in specs[:2])   # forces some streams to wait
-    rep = serve(specs, backend, budget_bytes=budget)
-    assert rep.frames == sum(len(s.arrivals_s) for s in specs) and rep.order_ok
-    assert rep.peak_bytes <= max(budget, max(backend.footprint(s) for s in specs))
-    for spec in specs:
-        f = frames[spec.sid]
-        with rs.Stream(backend.params(spec)) as st:
-            for k in range(len(spec.arrivals_s)):
-                if k == 0:
-                    st.full_frame(f["left"][0], f["right"][0])
-                else:
-                    st.reduced_frame(f["left"][k], f["right"][k], f["R"][k:k + 1], f["t"][k:k + 1], f["K"], 0.54)
-            alone = st.state()
-        for a, b in zip(alone, backend.finals[spec.sid]):
-            assert torch.equal(a, b), spec.sid
+        n = int(rng.integers(frames[0], frames[1]))
+        s = synth.kitti_like_sequence(800 + 10 * seed + i, n_frames=n, width=W, height=H, f=f, baseline=0.54,
+                                      device="cuda")
+        data[i] = dict(left=s["left"], right=s["right"], R=s["R"], t=s["t"], K=s["K"], baseline=0.54)
+        start = float(rng.uniform(0.0, spread))
+        specs.append(StreamSpec(i, W, H, D, start, poisson_arrivals(rng, start, float(rng.uniform(*rates)), n)))
+    return specs, data
+
+
+def _alone(rs, backend, spec, f):
+    with rs.Stream(backend.params(spec.geometry, 1)) as st:
+        if backend.cnn:
+            rs.rsgm_attach_cnn(st.handle, backend.cnn)
+        for k in range(len(spec.arrivals_s)):
+            if k == 0:
+                st.full_frame(f["left"][0], f["right"][0])
+            else:
+                st.reduced_frame(f["left"][k], f["right"][k], f["R"][k:k + 1], f["t"][k:k + 1], f["K"], 0.54)
+        return [x[0] for x in st.state()]
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_serving_results_equal_alone_results(rs, learned):
+    from paper_1809_07986_gb300 import learned as LO
+    from paper_1809_07986_gb300.serving import GpuBackend, serve
+    specs, frames = _mix(5, GEOMS[:4])
+    backend = GpuBackend(frames, network=LO.init_params(3) if learned else None)
+    try:
+        # room for two slots of the largest pool: some streams wait for a slot
+        budget = sum(backend.footprint(g, 1) for g in {s.geometry for s in specs}) + backend.footprint(
+            specs[0].geometry, 1)
+        rep = serve(specs, backend, budget_bytes=budget)
+        assert rep.frames == sum(len(s.arrivals_s) for s in specs) and rep.order_ok
+        assert rep.pool_bytes <= budget
+        for spec in specs:
+            for a, b in zip(_alone(rs, backend, spec, frames[spec.sid]), backend.finals[spec.sid]):
+                assert torch.equal(a, b), spec.sid
+    finally:
+        backend.close()
 
 
 def _oracle_final(orc, spec, f):
@@ -61,20 +84,10 @@ def _oracle_final(orc, spec, f):
 
 
 def test_served_streams_match_the_chained_oracle(rs, orc):
-    import synth
-    from paper_1809_07986_gb300.serving import GpuBackend, StreamSpec, poisson_arrivals, serve
-    rng = np.random.default_rng(11)
-    geoms = [(160, 120, 32, 100.0), (200, 100, 48, 150.0), (160, 120, 32, 100.0), (240, 96, 64, 200.0),
-             (200, 100, 48, 150.0), (160, 120, 32, 100.0)]
-    specs, frames = [], {}
-    for i, (W, H, D, f) in enumerate(geoms):
-        n = int(rng.integers(4, 8))
-        s = synth.kitti_like_sequence(800 + i, n_frames=n, width=W, height=H, f=f, baseline=0.54, device="cuda")
-        frames[i] = dict(left=s["left"], right=s["right"], R=s["R"], t=s["t"], K=s["K"], baseline=0.54)
-        start = float(rng.uniform(0.0, 0.05))
-        specs.append(StreamSpec(i, W, H, D, start, poisson_arrivals(rng, start, float(rng.uniform(20, 60)), n)))
+    from paper_1809_07986_gb300.serving import GpuBackend, serve
+    specs, frames = _mix(11, GEOMS)
     backend = GpuBackend(frames)
-    rep = serve(specs, backend, budget_bytes=sum(backend.footprint(s) for s in specs))
+    rep = serve(specs, backend, budget_bytes=10 ** 11)
     assert rep.frames == sum(len(s.arrivals_s) for s in specs) and rep.order_ok
     for spec in specs:
         o = _oracle_final(orc, spec, frames[spec.sid])
