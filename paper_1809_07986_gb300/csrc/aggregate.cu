@@ -11,7 +11,6 @@
 // lanes visit 4 consecutive pixels of one image row at every step).  Losses are held as two 16-bit values per 32-bit
 // register and combined with packed minima and carry-free 32-bit additions.
 #include "rsgm_internal.cuh"
-#include <stdlib.h>
 
 namespace rsgm {
 namespace {
@@ -479,8 +478,10 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     int words = (cap + 2 * plan.pad) / 2;
     if (!(words & 1)) ++words;
     plan.band_words = words;
+    // rows per horizontal warp: 16 measured fastest at 4 and 32 paper-shaped
+    // streams (8 lengthens the launch with more, emptier warps; 32 lengthens
+    // the 1242-step rows' critical path)
     plan.hlines = 16;
-    if (const char *e = getenv("RSGM_PROBE_HLINES")) plan.hlines = atoi(e);  // PROBE ONLY, not committed
     // Long lines first so that the tail of the launch is short: horizontal,
     // diagonal, vertical.  Planes are numbered by direction bit order.
     static const int order[8] = {0, 1, 4, 5, 6, 7, 2, 3};
