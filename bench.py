@@ -61,13 +61,10 @@ def parse():
                     help="path-sweep register capacity in cells for every handle (0: autotune each handle)")
     ap.add_argument("--handles", type=int, default=2,
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
-    ap.add_argument("--mixed", action="store_true",
-                    help="also time the mixed-resolution group (6x640x480/D64, 6x1242x375/D128, 4x1920x1080/D256)")
     ap.add_argument("--learned", action="store_true",
-                    help="also train the learned search window on 2000 frames of seeded 384x128 pairs and compare "
-                         "it with the fixed half-width 8 on held-out pairs")
-    ap.add_argument("--serve", action="store_true",
-                    help="also run the request loop: 32 Poisson streams (10-30 Hz) of 640x480/1242x375/1920x1080")
+                    help="train the learned search window on all 2000 frames of seeded 384x128 pairs (default: 512)")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the mixed-resolution group, learned-window and request-loop legs")
     ap.add_argument("--cpu-cores", type=int, default=0,
                     help="host cores for the oracle legs (0: every core this process may run on)")
     ap.add_argument("--no-extras", action="store_true",
@@ -350,10 +347,11 @@ def mixed_group(args, dev, stream):
 
 # ------------------------------------------------------------------ request loop
 
-def serving_loop(dev, nstreams=32, frames=20, budget_gb=48.0, seed=9):
+def serving_loop(dev, nstreams=32, frames=20, budget_gb=48.0, seed=9, network=None):
     """32 streams appear over one second, each a Poisson process at 10-30 Hz
     of a resolution drawn from {640x480/D64, 1242x375/D128, 1920x1080/D256};
-    admission by device footprint under a budget; first frame full range."""
+    pools sized by device footprint under a budget; a new stream's first frame
+    runs at full range; with `network`, the learned search window."""
     import numpy as np
     import synth
     from paper_1809_07986_gb300.serving import GpuBackend, StreamSpec, poisson_arrivals, serve
@@ -367,11 +365,66 @@ def serving_loop(dev, nstreams=32, frames=20, budget_gb=48.0, seed=9):
         data[i] = dict(left=s["left"], right=s["right"], R=s["R"], t=s["t"], K=s["K"], baseline=BASE)
         start = float(rng.uniform(0.0, 1.0))
         specs.append(StreamSpec(i, W_, H_, D_, start, poisson_arrivals(rng, start, float(rng.uniform(10, 30)), frames)))
-    backend = GpuBackend(data, device=dev)
-    rep = serve(specs, backend, budget_bytes=int(budget_gb * 1e9))
+    backend = GpuBackend(data, device=dev, network=network)
+    try:
+        rep = serve(specs, backend, budget_bytes=int(budget_gb * 1e9))
+    finally:
+        backend.close()
     out = rep.summary()
     out.update(streams=nstreams, frames_per_stream=frames, budget_gb=budget_gb, order_ok=rep.order_ok,
-               arrival="Poisson 10-30 Hz per stream, streams appearing over 1 s")
+               window="learned (trained network, fallback +-8)" if network is not None else "fixed +-4",
+               arrival="Poisson 10-30 Hz per stream, streams appearing over 1 s",
+               batching="one pool handle per resolution, each launch carrying every admitted stream's next "
+                        "arrived frame (rsgm_slot_frame)")
+    return out
+
+
+def path_ablation(dev, nstreams=8, nframes=11, radius=4):
+    """The paper's path ablation (Section 5, Table 2: 8 paths against 4
+    non-diagonal and 4 diagonal ones) on seeded paper-shaped sequences: for
+    each path set the reduced method and the full-range (plain) form run on
+    the same frames; reported per set are frames/s of the reduced form and
+    bad-pixel rates over frames 1..nframes-1, against the renderer's ground
+    truth (> 3 px and > 5 %, the KITTI outlier rule) and against the
+    full-range result of the same path set (> 3 px)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1809_07986_gb300 as rs
+    seqs = [synth.kitti_like_sequence(7000 + b, n_frames=100, width=W, height=H, f=F, baseline=BASE, device=dev,
+                                      render_frames=nframes) for b in range(nstreams)]
+    st = lambda k: torch.stack([q[k] for q in seqs], 1).contiguous()
+    L, R, gt, Rm, tv, K = st("left"), st("right"), st("disp"), st("R"), st("t"), seqs[0]["K"]
+    out = {}
+    for name, mask in (("8 paths", 0xFF), ("4 non-diagonal", 0x0F), ("4 diagonal", 0xF0)):
+        res = {}
+        for mode in (rs.RSGM_RADIUS_FIXED, rs.RSGM_RADIUS_FULL):
+            P = rs.rsgm_default_params(W, H, max_disp=D, radius=radius, batch=nstreams, path_mask=mask,
+                                       radius_mode=mode)
+            ds, ms = [], 0.0
+            with rs.Stream(P) as h:
+                h.full_frame(L[0], R[0])
+                for k in range(1, nframes):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    h.reduced_frame(L[k], R[k], Rm[k], tv[k], K, BASE)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    ds.append(h.state()[0].cpu().numpy())
+            res[mode] = (ds, nstreams * (nframes - 1) / (ms / 1e3))
+        red, full = res[rs.RSGM_RADIUS_FIXED][0], res[rs.RSGM_RADIUS_FULL][0]
+        g = gt[1:].cpu().numpy()
+
+        def kitti(d):
+            ok = g > 0
+            err = np.abs(np.stack(d) - g)
+            return float(((err > 3) & (err > 0.05 * g) & ok).sum() / ok.sum())
+
+        out[name] = {"frames_per_s": res[rs.RSGM_RADIUS_FIXED][1],
+                     "bad_vs_gt": kitti(red), "bad_vs_gt_full_range": kitti(full),
+                     "bad_vs_full_range": float((np.abs(np.stack(red) - np.stack(full)) > 3).mean())}
+    out["workload"] = "%d seeded 1242x375 streams, D=128, r=%d, reduced frames 1..%d" % (nstreams, radius, nframes - 1)
     return out
 
 
@@ -628,14 +681,19 @@ def run_ours(args, rank, world, local_rank):
                                "boxes_per_stream": float(np.mean(counts)),
                                "note": "3x3 median + integral image + windows on the GPU, grouping on the host"}
 
-        if args.mixed and rank == 0:
+        if rank == 0 and not args.no_next:
+            # the configurations past the paper's path: the mixed-resolution
+            # batch, the learned search window, the request loop
             result["mixed_group"] = mixed_group(args, dev, stream)
-        if args.serve and rank == 0:
-            result["serving"] = serving_loop(dev)
-        if args.learned and rank == 0:
             from paper_1809_07986_gb300 import learned
             with torch.cuda.device(dev):
-                result["learned_window"] = learned.run()
+                nt = 2000 if args.learned else 512
+                ev, theta = learned.run(train_frames=nt, eval_pairs=64, return_params=True)
+                ev["note"] = ("trained on %d frames (config: 2000; bench.py --learned trains on all 2000); "
+                              "held-out pairs, frame 1" % ev["train_frames"])
+                result["learned_window"] = ev
+                result["serving"] = serving_loop(dev, network=theta)
+            result["path_ablation"] = path_ablation(dev)
 
         if rank == 0:
             result["cpu_baseline"] = cpu_baseline(args, left, right, Rm, tv, K)

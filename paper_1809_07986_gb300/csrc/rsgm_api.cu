@@ -7,7 +7,10 @@
 
 #include <math.h>
 
+#include <algorithm>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "rsgm_internal.cuh"
 
@@ -707,9 +710,29 @@ int rsgm_detect(rsgm_stream s, const rsgm_detect_params *p, rsgm_box *boxes, int
         free(flags);
         return cuda_fail(e, "detection flags");
     }
-    for (int b = 0; b < g.B; ++b)
+    // the streams' groupings are independent: spread them over host threads
+    auto group = [&](int b) {
         counts[b] = group_boxes(flags + (size_t)b * dp.total, dp, p->iou_num, p->iou_den, p->min_area,
                                 capacity > 0 ? (int32_t *)(boxes + (size_t)b * capacity) : nullptr, capacity);
+    };
+    const int nt = std::min(g.B, (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 64u)));
+    if (nt <= 1) {
+        for (int b = 0; b < g.B; ++b) group(b);
+    } else {
+        std::vector<std::thread> pool;
+        pool.reserve(nt);
+        try {
+            for (int t = 0; t < nt; ++t)
+                pool.emplace_back([&, t] {
+                    for (int b = t; b < g.B; b += nt) group(b);
+                });
+        } catch (...) {
+            // a thread could not be started: its share runs here, below
+        }
+        for (std::thread &th : pool) th.join();
+        for (int t = (int)pool.size(); t < nt; ++t)
+            for (int b = t; b < g.B; b += nt) group(b);
+    }
     free(flags);
     return RSGM_OK;
 }

@@ -144,9 +144,10 @@ def evaluate(cnn, seeds, batch: int = 32, fixed_radius: int = 4, reps: int = 5, 
 
 
 def run(train_frames: int = 2000, eval_pairs: int = 64, batch: int = 32, lr: float = 3e-3, epochs: int = 1,
-        fixed_radius: int = 4):
+        fixed_radius: int = 4, return_params: bool = False):
     """Trains on train_frames / 2 pairs (two frames each) and evaluates on
-    held-out pairs against the fixed half-width and the untrained network."""
+    held-out pairs against the fixed half-width and the untrained network.
+    Returns the report, and with return_params also the trained parameters."""
     t0 = time.perf_counter()
     seeds = list(range(10_000, 10_000 + train_frames // 2))
     cnn, theta, losses = train(seeds, batch=batch, lr=lr, epochs=epochs)
@@ -161,4 +162,4 @@ def run(train_frames: int = 2000, eval_pairs: int = 64, batch: int = 32, lr: flo
         B.rsgm_cnn_destroy(untrained)
     ev.update(train_frames=2 * len(seeds) * epochs, train_s=t1 - t0, loss_first=losses[0] if losses else None,
               loss_last=losses[-1] if losses else None, steps=len(losses))
-    return ev
+    return (ev, theta) if return_params else ev

@@ -214,3 +214,25 @@ def test_training_driver_runs_end_to_end(rs):
         assert ev[k]["frames_per_s"] > 0 and 0.0 <= ev[k]["bad_pixel_rate_gt"] <= 1.0
         assert 0.0 <= ev[k]["bad_vs_full"] <= 1.0 and ev[k]["cells_per_frame"] > 0
     assert ev["full"]["bad_vs_full"] == 0.0 and ev["fixed_radius"] == 4
+
+
+def test_trained_network_gains_over_the_untrained_network_and_the_fixed_window(rs):
+    # 512 training frames (16 steps of 32 pairs' frames), then held-out pairs:
+    # the trained network searches fewer cells than the untrained one (which
+    # falls back to +-8 almost everywhere) and than the fixed +-4 window of the
+    # tiny configuration, with at most 0.5 percentage points more pixels that
+    # differ from the full-range result by more than 3 px.
+    from paper_1809_07986_gb300 import learned
+    cnn, theta, losses = learned.train(list(range(10_000, 10_256)), batch=32)
+    untrained = rs.rsgm_cnn_create(learned.init_params(0), torch.cuda.current_stream())
+    try:
+        ev = learned.evaluate(cnn, range(90_000, 90_064), batch=32, reps=1, fixed_radius=4, untrained=untrained)
+    finally:
+        rs.rsgm_cnn_destroy(cnn)
+        rs.rsgm_cnn_destroy(untrained)
+    print({k: (round(v["cells_per_frame"]), round(100 * v["bad_vs_full"], 3)) for k, v in ev.items()
+           if isinstance(v, dict)})
+    assert losses[-1] < 0.5 * losses[0]
+    assert ev["learned"]["cells_per_frame"] < 0.6 * ev["untrained"]["cells_per_frame"]
+    assert ev["learned"]["cells_per_frame"] < 0.8 * ev["fixed"]["cells_per_frame"]
+    assert ev["learned"]["bad_vs_full"] <= ev["fixed"]["bad_vs_full"] + 0.005
