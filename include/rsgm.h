@@ -324,9 +324,11 @@ int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t 
 /*
  * Schedule autotuner.  The aggregation kernel walks one path line per lane;
  * a lane keeps windows of up to a "register capacity" of cells in registers
- * and leaves wider ones to its whole warp.  rsgm_autotune times the kernel
- * on the handle's latest frame with each capacity (2, 6, 10, 18 cells) and
- * keeps the fastest for later frames (written to *cells if not NULL).
+ * and leaves wider ones to its whole warp; a warp walks 32 vertical or
+ * diagonal lines and 8, 16 or 32 rows.  rsgm_autotune times the kernel on the
+ * handle's latest frame with each capacity (2, 6, 10, 18 cells) and row count
+ * and keeps the fastest for later frames (the capacity is written to *cells
+ * if not NULL).
  * Results do not depend on the choice; only speed does.  Requires a
  * processed frame; synchronises.
  */
@@ -334,7 +336,8 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells);
 
 /* Sets the register capacity by hand: 0 = the radius mode's default
  * (2 radius + 1 for fixed windows), else 1 .. 32 cells, rounded up to the
- * nearest of 2, 6, 10, 18.  Results do not depend on it. */
+ * nearest of 2, 6, 10, 18; the row count returns to its default (16).
+ * Results do not depend on it. */
 int rsgm_set_schedule(rsgm_stream s, int32_t cells);
 
 /*

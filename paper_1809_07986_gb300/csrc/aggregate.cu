@@ -75,6 +75,30 @@ __device__ __forceinline__ void band_load(const unsigned *band, int t, int pad, 
     }
 }
 
+// Byte bands (the cheap masking, where 0xFF acts as +inf): slot s is byte
+// s + pad of the band.  n packed pairs starting at slot t (any alignment).
+template <int N>
+__device__ __forceinline__ void band_load8(const unsigned *band, int t, int pad, unsigned (&u)[N])
+{
+    const int s = t + pad;
+    const unsigned *p = band + (s >> 2);
+    const unsigned sh = 8u * (unsigned)(s & 3);
+    constexpr int NWORDS = (2 * N + 3) / 4;  // aligned words of the 2N bytes
+    unsigned w0 = p[0];
+#pragma unroll
+    for (int j = 0; j < NWORDS; ++j) {
+        const unsigned w1 = p[j + 1];
+        const unsigned a = __funnelshift_r(w0, w1, sh);
+        if (2 * j < N) u[2 * j] = __byte_perm(a, 0u, 0x4140u);
+        if (2 * j + 1 < N) u[2 * j + 1] = __byte_perm(a, 0u, 0x4342u);
+        w0 = w1;
+    }
+}
+
+// A pair saturated to 0xFF per half (a loss of at least 0xFF acts as +inf
+// under the cheap masking, so saturating keeps every result).
+__device__ __forceinline__ unsigned sat8(unsigned x) { return vmin2(x, 0x00FF00FFu); }
+
 // Walks 32 adjacent lines of one direction.
 //
 // Narrow pixels (window width <= 2 NR) are done by the line's own lane, the
@@ -137,6 +161,21 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
     int plo = 0, pw = 0, pm = 0;  // predecessor window and minimum; pw = 0: no predecessor
     bool inband = false;          // the predecessor's losses are in the band, not in P
 
+    // the lane's narrow window into its band at slots [0, 2 NR), +inf after it
+    auto spill = [&](const unsigned (&Pr)[NR]) {
+        if (kCheap) {
+            constexpr int NQ = (NR + 1) / 2;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                band[(pad >> 2) + q] = pack4(sat8(Pr[2 * q]), 2 * q + 1 < NR ? sat8(Pr[2 * q + 1]) : 0x00FF00FFu);
+            for (int q = 0; q < (pad >> 2); ++q) band[(pad >> 2) + NQ + q] = 0xFFFFFFFFu;
+        } else {
+#pragma unroll
+            for (int i = 0; i < NR; ++i) band[(pad >> 1) + i] = Pr[i];
+            for (int q = 0; q < (pad >> 1); ++q) band[(pad >> 1) + NR + q] = kInf2;
+        }
+    };
+
     // This lane's cost words of the first pass over the wide windows among
     // the pixels of `m`: the first two wide pixels, one per half-warp, 8
     // cells per lane and 128-cell pass.
@@ -195,15 +234,16 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
                 if (inband || e < -3 || e > 1) {
                     if (!inband) {
                         // realign a large move through the band
-#pragma unroll
-                        for (int i = 0; i < NR; ++i) band[(pad >> 1) + i] = P[i];
-                        for (int q = 0; q < (pad >> 1); ++q) band[(pad >> 1) + NR + q] = kInf2;
+                        spill(P);
                     }
                     if (e >= pw || e + NC + 1 < 0) {
 #pragma unroll
                         for (int i = 0; i <= NR; ++i) U[i] = kInf2;
                     } else {
-                        band_load<NR + 1>(band, e, pad, U);
+                        if (kCheap)
+                            band_load8<NR + 1>(band, e, pad, U);
+                        else
+                            band_load<NR + 1>(band, e, pad, U);
                     }
                 } else {
                     // e = 2 sh + odd with sh in {-2, -1, 0}: U[i] = Q[i + sh],
@@ -254,9 +294,7 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
         unsigned wide = __ballot_sync(kFull, w > NC);
         if (wide) {
             if (w > NC && pw > 0 && !inband) {
-#pragma unroll
-                for (int i = 0; i < NR; ++i) band[(pad >> 1) + i] = P[i];
-                for (int q = 0; q < (pad >> 1); ++q) band[(pad >> 1) + NR + q] = kInf2;
+                spill(P);
             }
             __syncwarp();
             const int half = lane >> 4, hl = lane & 15;
@@ -290,7 +328,10 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
 #pragma unroll
                             for (int i = 0; i < 5; ++i) U[i] = kInf2;
                         } else {
-                            band_load<5>(sbd, t0, pad, U);
+                            if (kCheap)
+                                band_load8<5>(sbd, t0, pad, U);
+                            else
+                                band_load<5>(sbd, t0, pad, U);
                         }
                         unsigned cw0, cw1;  // the first pass's costs were fetched a step ahead
                         if (jp == 0) {
@@ -314,6 +355,7 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             Lr[it][i] = eq1(U[i], U[i + 1], c[i], P1x2, cap2, m2);
+                            if (kCheap) Lr[it][i] = sat8(Lr[it][i]);  // byte bands: saturated
                             run = vmin2(run, Lr[it][i]);
                         }
                         if (sizeof(T) == 1) {
@@ -339,17 +381,27 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
                     if (c0 < sw) {
                         // 32-bit stores: bands have an odd word stride, so a
                         // band word is not 8-byte aligned in general
-                        unsigned *q = sbd + ((c0 + pad) >> 1);
-                        q[0] = Lr[it][0];
-                        q[1] = Lr[it][1];
-                        if (c0 + 4 < sw) {
-                            q[2] = Lr[it][2];
-                            q[3] = Lr[it][3];
+                        if (kCheap) {
+                            unsigned *q = sbd + ((c0 + pad) >> 2);
+                            q[0] = pack4(Lr[it][0], Lr[it][1]);
+                            if (c0 + 4 < sw) q[1] = pack4(Lr[it][2], Lr[it][3]);
+                        } else {
+                            unsigned *q = sbd + ((c0 + pad) >> 1);
+                            q[0] = Lr[it][0];
+                            q[1] = Lr[it][1];
+                            if (c0 + 4 < sw) {
+                                q[2] = Lr[it][2];
+                                q[3] = Lr[it][3];
+                            }
                         }
                     }
                 }
                 const int ext = (sw + 3) & ~3;
-                if (mine && hl < (pad >> 1)) sbd[((ext + pad) >> 1) + hl] = kInf2;
+                if (kCheap) {
+                    if (mine && hl < (pad >> 2)) sbd[((ext + pad) >> 2) + hl] = 0xFFFFFFFFu;
+                } else {
+                    if (mine && hl < (pad >> 1)) sbd[((ext + pad) >> 1) + hl] = kInf2;
+                }
                 __syncwarp();
                 if (lane == sa || lane == sb) {  // the sources take their own window
                     plo = lo;
@@ -378,7 +430,7 @@ __constant__ int kDX[8] = {+1, -1, 0, 0, +1, -1, -1, +1};
 __constant__ int kDY[8] = {0, 0, +1, -1, +1, -1, +1, -1};
 
 template <typename T, int NR, int KW, bool kCheap>
-__global__ void __launch_bounds__(kLineWarps * 32, 5)
+__global__ void __launch_bounds__(kLineWarps * 32, (kCheap && KW == 1) ? 8 : 5)
     k_lines(const uint8_t *__restrict__ cost, T *__restrict__ planes, const uint2 *__restrict__ meta,
             const __grid_constant__ LinePlan plan)
 {
@@ -407,7 +459,11 @@ __global__ void __launch_bounds__(kLineWarps * 32, 5)
     const bool line_ok = li < nl && lane < lpw;
     unsigned *band_all = smem + warp * 32 * plan.band_words;
     unsigned *band = band_all + lane * plan.band_words;
-    for (int q = 0; q < (plan.pad >> 1); ++q) band[q] = kInf2;  // slots [-pad, 0): always +inf
+    // slots [-pad, 0): always +inf
+    if (kCheap)
+        for (int q = 0; q < (plan.pad >> 2); ++q) band[q] = 0xFFFFFFFFu;
+    else
+        for (int q = 0; q < (plan.pad >> 1); ++q) band[q] = kInf2;
     __syncwarp();
     T *plane = planes + (long long)plan.plane_of[si] * plan.plane_stride;
     walk<T, NR, KW, kCheap>(dx, dy, b, kbase + li, line_ok, cost, plane, meta, plan, band_all, band);
@@ -459,7 +515,7 @@ int sweep_capacity(int cells)
 }
 
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2, int nbits,
-                         int plane_bytes, int capacity, cudaStream_t st)
+                         int plane_bytes, int capacity, int hlines, cudaStream_t st)
 {
     LinePlan plan;
     plan.g = g;
@@ -467,21 +523,23 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     plan.P2 = P2;
     plan.plane_stride = plane_stride(g);
     const int nr = sweep_capacity(capacity) / 2;
+    // the cheap masking (cells past a window cost 0xFF) needs every cap
+    // m + P2 <= nbits + 2 P2 below 0xFF; its losses then fit byte bands
+    const bool cheap = plane_bytes == 1 && nbits + 2 * P2 < 255;
     // +inf padding around a band's window: at least the widest read past it
-    // (a narrow read spans 2 NR + 2 slots, a wide one 10), even so that slot 0
-    // is word aligned, and at most 32 words (one store per lane)
-    const int pad = max(10, 2 * nr + 2);
-    plan.pad = (pad + 1) & ~1;
+    // (a narrow read spans 2 NR + 2 slots, a wide one 10), a multiple of 4 so
+    // that slot 0 is word aligned in byte and in 16-bit bands
+    plan.pad = (max(10, 2 * nr + 2) + 3) & ~3;
     // slots [-pad, round4(max(D, 2 NR)) + pad) in 32-bit words, an odd count
     // so that the lanes' bands fall in different shared-memory banks
     const int cap = (max(g.D, 2 * nr) + 3) & ~3;
-    int words = (cap + 2 * plan.pad) / 2;
+    int words = cheap ? (cap + 2 * plan.pad + 3) / 4 : (cap + 2 * plan.pad) / 2;
     if (!(words & 1)) ++words;
     plan.band_words = words;
-    // rows per horizontal warp: 16 measured fastest at 4 and 32 paper-shaped
-    // streams (8 lengthens the launch with more, emptier warps; 32 lengthens
-    // the 1242-step rows' critical path)
-    plan.hlines = 16;
+    // rows per horizontal warp: 16 by default (fastest at 4 and 32
+    // paper-shaped streams: 8 adds emptier warps, 32 lengthens the 1242-step
+    // rows' critical path); the autotuner tries 8, 16 and 32
+    plan.hlines = hlines == 8 || hlines == 32 ? hlines : 16;
     // Long lines first so that the tail of the launch is short: horizontal,
     // diagonal, vertical.  Planes are numbered by direction bit order.
     static const int order[8] = {0, 1, 4, 5, 6, 7, 2, 3};
@@ -500,9 +558,6 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
         plan.warp_begin[plan.ndir + 1] = plan.warp_begin[plan.ndir] + warps;
         plan.ndir++;
     }
-    // the cheap masking (cells past a window cost 0xFF) needs every cap
-    // m + P2 <= nbits + 2 P2 below 0xFF
-    const bool cheap = plane_bytes == 1 && nbits + 2 * P2 < 255;
     if (plane_bytes == 1)
         return cheap ? launch_t<uint8_t, true>(b, plan, nr, st) : launch_t<uint8_t, false>(b, plan, nr, st);
     return launch_t<uint16_t, false>(b, plan, nr, st);

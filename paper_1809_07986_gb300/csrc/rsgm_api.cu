@@ -36,6 +36,7 @@ struct rsgm_stream_s {
     int capacity;     // window cells a path-sweep lane keeps in registers (default for the radius mode)
     int sm_count;     // multiprocessors of the handle's device
     int tuned_cap;    // register capacity picked by rsgm_autotune / rsgm_set_schedule (0: default)
+    int tuned_hl;     // rows per horizontal warp picked by rsgm_autotune (0: default)
     bool capturing;   // enqueueing into a group's graph: no stage-timing events
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
@@ -250,7 +251,7 @@ int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool c
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
     RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes,
-                           s->tuned_cap ? s->tuned_cap : s->capacity, s->st));
+                           s->tuned_cap ? s->tuned_cap : s->capacity, s->tuned_hl, s->st));
     RSGM_MARK(s, 5);
     RSGM_CUDA(launch_update(s->buf, g, fp, r_map, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
@@ -1015,6 +1016,7 @@ int rsgm_set_schedule(rsgm_stream s, int32_t cells)
     if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
     if (cells < 0 || cells > 32) return fail(RSGM_ERR_INVALID_ARG, "schedule (register capacity) in [0, 32]");
     s->tuned_cap = cells ? sweep_capacity(cells) : 0;
+    s->tuned_hl = 0;
     return RSGM_OK;
 }
 
@@ -1030,21 +1032,22 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells)
         cudaEventDestroy(e0);
         return fail(RSGM_ERR_CUDA, "cudaEventCreate");
     }
-    // candidates: the instantiated register capacities
-    const int cands[4] = {2, 6, 10, 18};
-    const int nc = 4;
-    int best = 0;
+    // candidates: the instantiated register capacities, and 8, 16 or 32 rows
+    // per horizontal warp
+    const int caps[4] = {2, 6, 10, 18}, hls[3] = {8, 16, 32};
+    const int nc = 12;
+    int best = 0, best_hl = 0;
     float best_ms = 0.0f;
     int rc = RSGM_OK;
     // Every candidate computes the same planes (each schedule is exact), so
     // re-running the aggregation on the last frame's costs changes nothing.
     for (int ci = 0; ci < nc && rc == RSGM_OK; ++ci) {
-        const int cand = cands[ci];
+        const int cand = caps[ci / 3], hl = hls[ci % 3];
         float ms = 1e30f;
         for (int rep = 0; rep < 3 && rc == RSGM_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, s->st);
             if (e == cudaSuccess)
-                e = launch_paths(s->buf, s->g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes, cand,
+                e = launch_paths(s->buf, s->g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes, cand, hl,
                                  s->st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1055,6 +1058,7 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells)
         }
         if (rc == RSGM_OK && (best == 0 || ms < best_ms)) {
             best = cand;
+            best_hl = hl;
             best_ms = ms;
         }
     }
@@ -1062,6 +1066,7 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells)
     cudaEventDestroy(e1);
     if (rc) return rc;
     s->tuned_cap = best;
+    s->tuned_hl = best_hl;
     if (cells) *cells = best;
     return RSGM_OK;
 }

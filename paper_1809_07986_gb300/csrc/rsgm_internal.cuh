@@ -179,9 +179,10 @@ cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStre
 // planes of `plane_bytes` (1 or 2) per cell.  Windows of up to `capacity`
 // cells (rounded up by sweep_capacity to 2, 6, 10 or 18) are walked in a
 // lane's registers, wider ones by the whole warp.
+// hlines: rows a warp walks for the horizontal directions (8, 16 or 32; 0 = 16).
 int sweep_capacity(int cells);
 cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2, int nbits,
-                         int plane_bytes, int capacity, cudaStream_t st);
+                         int plane_bytes, int capacity, int hlines, cudaStream_t st);
 
 // Sum of the planes, winner-takes-all, Kalman correction and gate
 // (Sections 2.2-2.4).
