@@ -340,6 +340,10 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells);
  * Results do not depend on it. */
 int rsgm_set_schedule(rsgm_stream s, int32_t cells);
 
+/* Sets the rows a warp walks for the horizontal directions: 8, 16 or 32
+ * (0 = the default, 16).  Results do not depend on it. */
+int rsgm_set_rows_per_warp(rsgm_stream s, int32_t rows);
+
 /*
  * A group advances several handles of possibly different geometry by one
  * reduced frame each in a single CUDA graph launch: every member's launches

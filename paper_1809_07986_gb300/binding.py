@@ -122,6 +122,7 @@ SIGNATURES = {
     "rsgm_window_offsets_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "rsgm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "rsgm_set_rows_per_warp": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rsgm_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32]),
     "rsgm_group_reduced_frame": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                                 ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
@@ -351,6 +352,10 @@ def rsgm_autotune(h: int) -> int:
 
 def rsgm_set_schedule(h: int, cells: int):
     _check(lib().rsgm_set_schedule(h, cells), "rsgm_set_schedule")
+
+
+def rsgm_set_rows_per_warp(h: int, rows: int):
+    _check(lib().rsgm_set_rows_per_warp(h, rows), "rsgm_set_rows_per_warp")
 
 
 def rsgm_group_create(handles) -> int:

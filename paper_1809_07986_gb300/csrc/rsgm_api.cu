@@ -425,7 +425,7 @@ int rsgm_footprint(const rsgm_params *p, uint64_t *bytes)
     const uint64_t plane_bytes = nbits + p->P2 <= 255 ? 1 : 2;
     const uint64_t stride = (cells + 15) / 16 * 16;
     const uint64_t per_pixel = 2 + 16 + 8 + 8 + 8 + 4 + 1 + 4 + 8 + 2 + 1 + 4 + 4 + 4 + RSGM_MAX_WINDOW_SIZES;
-    *bytes = n * per_pixel + cells * (1 + 2) + 128 + stride * __builtin_popcount(p->path_mask) * plane_bytes +
+    *bytes = n * per_pixel + cells * (1 + 2) + 128 + 32 + (stride * __builtin_popcount(p->path_mask) + 16) * plane_bytes +
              (uint64_t)p->batch * p->height * 12 + (uint64_t)p->batch * (p->height + 1) * (p->width + 1) * 8 + 32 +
              (p->radius_mode == RSGM_RADIUS_LEARNED ? n * 261 : 0);
     return RSGM_OK;
@@ -483,8 +483,9 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc(&b.meta, n, all, nall)) || (rc = alloc(&b.row_total, rows, all, nall)) ||
         (rc = alloc(&b.row_base, rows, all, nall)) || (rc = alloc(&b.row_cells, rows, all, nall)) ||
         (rc = alloc(&b.cost, cells + 128, all, nall)) ||  // + the path sweep's prefetch past the last window (< 128 B)
-        (rc = alloc((uint8_t **)&b.planes, (size_t)plane_stride(s->g) * s->nplanes * s->plane_bytes, all, nall)) ||
-        (rc = alloc(&b.S, cells, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
+        // + 16 cells: the update kernel reads and writes whole 16-cell chunks
+        (rc = alloc((uint8_t **)&b.planes, ((size_t)plane_stride(s->g) * s->nplanes + 16) * s->plane_bytes, all, nall)) ||
+        (rc = alloc(&b.S, cells + 16, all, nall)) || (rc = alloc(&b.d_int, n, all, nall)) ||
         (rc = alloc(&b.mask, n, all, nall)) || (rc = alloc(&b.d_z, n, all, nall)) ||
         (rc = alloc(&b.nu, n, all, nall)) || (rc = alloc(&b.counters, 4, all, nall)) ||
         (rc = alloc(&b.median, n, all, nall)) ||
@@ -1017,6 +1018,15 @@ int rsgm_set_schedule(rsgm_stream s, int32_t cells)
     if (cells < 0 || cells > 32) return fail(RSGM_ERR_INVALID_ARG, "schedule (register capacity) in [0, 32]");
     s->tuned_cap = cells ? sweep_capacity(cells) : 0;
     s->tuned_hl = 0;
+    return RSGM_OK;
+}
+
+int rsgm_set_rows_per_warp(rsgm_stream s, int32_t rows)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    if (rows != 0 && rows != 8 && rows != 16 && rows != 32)
+        return fail(RSGM_ERR_INVALID_ARG, "rows per warp must be 0, 8, 16 or 32");
+    s->tuned_hl = rows;
     return RSGM_OK;
 }
 

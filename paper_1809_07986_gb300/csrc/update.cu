@@ -17,49 +17,45 @@ constexpr int kLaneScan = 16;      // windows up to this width are scanned by th
 constexpr unsigned kFull = 0xffffffffu;
 
 // S = sum of the direction planes over the cells [c0, c1), written to S and to
-// the warp's staging buffer (indexed from c0).  8-bit planes are read four
-// cells per 32-bit load (planes start 16-element aligned; the aligned words
-// around the span stay inside the plane allocation) and summed as two 16-bit
-// pairs, which cannot carry: 8 planes x 255 < 2^16.
+// the warp's staging buffer (indexed from a16 = c0 rounded down to 16 cells).
+// 8-bit planes are read 16 cells per 128-bit load and summed as 16-bit pairs,
+// which cannot carry: 8 planes x 255 < 2^16.  The whole chunks cover cells of
+// the neighbouring warps' spans as well: S there is the same sum of the same
+// planes, so writing it again changes nothing.  (Planes start 16-element
+// aligned, and the planes and S have 16 cells of slack past the last one.)
 __device__ __forceinline__ void sum_planes(const uint8_t *__restrict__ planes, long long stride, int nplanes,
                                            unsigned c0, unsigned c1, uint16_t *__restrict__ S,
                                            uint16_t *stage, int lane)
 {
-    constexpr int kWordsPerLane = 4;  // all loads of a batch are issued before any is used
-    const unsigned a0 = c0 & ~3u;
-    const int nwords = (int)((c1 - a0 + 3) >> 2);
-    for (int base = 0; base < nwords; base += 32 * kWordsPerLane) {
-        unsigned even[kWordsPerLane], odd[kWordsPerLane];
-#pragma unroll
-        for (int u = 0; u < kWordsPerLane; ++u) even[u] = odd[u] = 0;
+    const unsigned a16 = c0 & ~15u;
+    const int nchunks = (int)((c1 - a16 + 15) >> 4);
+    for (int ci = lane; ci < nchunks; ci += 32) {
+        const unsigned cell = a16 + 16u * (unsigned)ci;
+        uint4 ev = make_uint4(0u, 0u, 0u, 0u), od = ev;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             if (q < nplanes) {
-#pragma unroll
-                for (int u = 0; u < kWordsPerLane; ++u) {
-                    const int wi = base + u * 32 + lane;
-                    if (wi < nwords) {
-                        const unsigned v = *(const unsigned *)(planes + q * stride + a0 + 4u * (unsigned)wi);
-                        even[u] += v & 0x00FF00FFu;
-                        odd[u] += (v >> 8) & 0x00FF00FFu;
-                    }
-                }
+                const uint4 v = *(const uint4 *)(planes + q * stride + cell);
+                ev.x += v.x & 0x00FF00FFu;
+                od.x += (v.x >> 8) & 0x00FF00FFu;
+                ev.y += v.y & 0x00FF00FFu;
+                od.y += (v.y >> 8) & 0x00FF00FFu;
+                ev.z += v.z & 0x00FF00FFu;
+                od.z += (v.z >> 8) & 0x00FF00FFu;
+                ev.w += v.w & 0x00FF00FFu;
+                od.w += (v.w >> 8) & 0x00FF00FFu;
             }
         }
-#pragma unroll
-        for (int u = 0; u < kWordsPerLane; ++u) {
-            const int wi = base + u * 32 + lane;
-            if (wi >= nwords) continue;
-            const unsigned cell = a0 + 4u * (unsigned)wi;
-            const unsigned s[4] = {even[u] & 0xFFFFu, odd[u] & 0xFFFFu, even[u] >> 16, odd[u] >> 16};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const unsigned c = cell + j;
-                if (c >= c0 && c < c1) {
-                    S[c] = (uint16_t)s[j];
-                    if (stage) stage[c - c0] = (uint16_t)s[j];
-                }
-            }
+        // word j of a chunk holds cells 4j .. 4j+3: (even lo, odd lo, even hi, odd hi)
+        const uint4 sa = make_uint4(__byte_perm(ev.x, od.x, 0x5410u), __byte_perm(ev.x, od.x, 0x7632u),
+                                    __byte_perm(ev.y, od.y, 0x5410u), __byte_perm(ev.y, od.y, 0x7632u));
+        const uint4 sb = make_uint4(__byte_perm(ev.z, od.z, 0x5410u), __byte_perm(ev.z, od.z, 0x7632u),
+                                    __byte_perm(ev.w, od.w, 0x5410u), __byte_perm(ev.w, od.w, 0x7632u));
+        *(uint4 *)(S + cell) = sa;
+        *(uint4 *)(S + cell + 8) = sb;
+        if (stage) {
+            *(uint4 *)(stage + (cell - a16)) = sa;
+            *(uint4 *)(stage + (cell - a16) + 8) = sb;
         }
     }
 }
@@ -74,7 +70,7 @@ __device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, 
         for (int q = 0; q < 8; ++q)
             if (q < nplanes) v += planes[q * stride + c];
         S[c] = (uint16_t)v;
-        if (stage) stage[c - c0] = (uint16_t)v;
+        if (stage) stage[c - (c0 & ~15u)] = (uint16_t)v;
     }
 }
 
@@ -93,7 +89,7 @@ __device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, 
 // reset to the measurement, else K = p_pred / (p_pred + r), d = d_pred + K nu,
 // p = (1 - K)^2 p_pred + K^2 r.
 template <typename T>
-__global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__ planes, long long plane_stride,
+__global__ void __launch_bounds__(kUpdWarps * 32, 12) k_update(const T *__restrict__ planes, long long plane_stride,
                                                         int nplanes, uint16_t *__restrict__ S,
                                                         const uint2 *__restrict__ meta,
                                                         const uint8_t *__restrict__ cls,
@@ -116,11 +112,12 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
     const unsigned span0 = __shfl_sync(0xffffffffu, m.x, 0);
     const int nvalid = (int)min(32LL, g.NPIX - gi0);
     const unsigned last_end = __shfl_sync(0xffffffffu, m.x + (unsigned)w, nvalid - 1);
-    const bool staged = last_end - span0 <= (unsigned)kStageCells;
+    const unsigned a16 = span0 & ~15u;  // the staging buffer starts at the span's 16-cell chunk
+    const bool staged = last_end - a16 <= (unsigned)kStageCells;
     uint16_t *stage = staged ? sS + warp * kStageCells : nullptr;
     sum_planes(planes, plane_stride, nplanes, span0, last_end, S, stage, lane);
     __syncwarp();  // S (shared or global) complete for the warp
-    const uint16_t *s = staged ? stage + (m.x - span0) : S + m.x;
+    const uint16_t *s = staged ? stage + (m.x - a16) : S + m.x;
     int best = 0;
     unsigned bs = 0;
     if (valid && w > 0 && w <= kLaneScan) {
@@ -140,7 +137,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) k_update(const T *__restrict__
             wide &= wide - 1;
             const unsigned off = __shfl_sync(kFull, m.x, src);
             const int ww = __shfl_sync(kFull, w, src);
-            const uint16_t *s2 = staged ? stage + (off - span0) : S + off;
+            const uint16_t *s2 = staged ? stage + (off - a16) : S + off;
             unsigned key = 0xFFFFFFFFu;  // S in the high half, k in the low: the first minimum wins
             for (int k = lane; k < ww; k += 32) key = min(key, ((unsigned)s2[k] << 16) | (unsigned)k);
             key = __reduce_min_sync(kFull, key);

@@ -252,10 +252,22 @@ class GpuBackend(Backend):
         return token.query()
 
     def release(self, h, slot, spec):
-        with self.torch.cuda.stream(h["stream"]):
-            self.finals[spec.sid] = tuple(x[slot].clone() for x in h["st"].state(device=self.device))
+        # copied out on the pool's CUDA stream, behind the stream's last
+        # launch and ahead of the slot's next occupant: the loop does not wait
+        torch = self.torch
+        B, H, W = h["st"].shape
+        with torch.cuda.stream(h["stream"]):
+            d = torch.empty(B, H, W, dtype=torch.float32, device=self.device)
+            p = torch.empty_like(d)
+            m = torch.empty(B, H, W, dtype=torch.uint8, device=self.device)
+            di = torch.empty(B, H, W, dtype=torch.int16, device=self.device)
+            self.rs.rsgm_state(h["st"].handle, d, p, m, di)
+            # the slot's share only, cloned on the same stream; the pool-wide
+            # copies return to the allocator, which reuses them in stream order
+            self.finals[spec.sid] = tuple(x[slot].clone() for x in (d, p, m, di))
 
     def close_pool(self, h):
+        h["st"].sync()  # the state copies are complete before the handle goes
         h["st"].close()
 
     def close(self):

@@ -153,6 +153,37 @@ def test_group_rejects_host_images_and_mixed_streams(rs):
             rs.rsgm_group_destroy(g)
 
 
+@pytest.mark.parametrize("mask", [0x01, 0x02, 0x0F])
+def test_every_row_schedule_gives_the_same_aggregation(rs, mask):
+    # rows per horizontal warp (8, 16, 32) and register capacities, for one
+    # horizontal direction alone and for both (a row pair)
+    B, W, H, D, f = 2, 240, 100, 64, 150.0
+    import synth
+    seqs = [synth.kitti_like_sequence(720 + b, n_frames=3, width=W, height=H, f=f, baseline=0.54) for b in range(B)]
+    st = lambda k: torch.stack([q[k] for q in seqs])
+    L, R, Rm, t, K = st("left"), st("right"), st("R"), st("t"), seqs[0]["K"]
+    P = rs.rsgm_default_params(W, H, max_disp=D, radius=4, batch=B, path_mask=mask)
+    results = {}
+    for cells in (0, 2, 18):
+        for rows in (0, 8, 32):
+            with rs.Stream(P) as s:
+                rs.rsgm_set_schedule(s.handle, cells)
+                rs.rsgm_set_rows_per_warp(s.handle, rows)
+                s.full_frame(L[:, 0].cuda().contiguous(), R[:, 0].cuda().contiguous())
+                for k in (1, 2):
+                    s.reduced_frame(L[:, k].cuda().contiguous(), R[:, k].cuda().contiguous(), Rm[:, k].contiguous(),
+                                    t[:, k].contiguous(), K, 0.54)
+                results[(cells, rows)] = [s.read(rs.RSGM_BUF_AGGREGATED, torch.int16)] + [x.cpu() for x in s.state()]
+    base = results[(0, 0)]
+    for key, got in results.items():
+        for u, v in zip(base, got):
+            assert torch.equal(u, v), key
+    with rs.Stream(P) as s:
+        with pytest.raises(rs.RsgmError) as e:
+            rs.rsgm_set_rows_per_warp(s.handle, 12)
+        assert e.value.code == rs.RSGM_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("radius", [2, 4, 8])
 def test_every_schedule_gives_the_same_aggregation(rs, radius):
     # Eq. 1 is exact in integers, so S and the state must not depend on how
