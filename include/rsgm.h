@@ -325,10 +325,11 @@ int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t 
  * Schedule autotuner.  The aggregation kernel walks one path line per lane;
  * a lane keeps windows of up to a "register capacity" of cells in registers
  * and leaves wider ones to its whole warp; a warp walks 32 vertical or
- * diagonal lines and 8, 16 or 32 rows.  rsgm_autotune times the kernel on the
- * handle's latest frame with each capacity (2, 6, 10, 18 cells) and row count
- * and keeps the fastest for later frames (the capacity is written to *cells
- * if not NULL).
+ * diagonal lines.  The rows go to a row sweep or to the line sweep (see
+ * rsgm_set_rows_per_warp).  rsgm_autotune times the aggregation on the
+ * handle's latest frame with each capacity (2, 6, 10, 18 cells) and each way
+ * of sweeping the rows and keeps the fastest for later frames (the capacity
+ * is written to *cells if not NULL).
  * Results do not depend on the choice; only speed does.  Requires a
  * processed frame; synchronises.
  */
@@ -340,8 +341,10 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells);
  * Results do not depend on it. */
 int rsgm_set_schedule(rsgm_stream s, int32_t cells);
 
-/* Sets the rows a warp walks for the horizontal directions: 8, 16 or 32
- * (0 = the default, 16).  Results do not depend on it. */
+/* How the horizontal directions are swept: 0 (the default) by the row
+ * sweep, G lanes sharing each row, on a stream of the handle's own that runs
+ * beside the other directions' sweep; 8, 16 or 32 by the line sweep with
+ * that many rows per warp.  Results do not depend on it. */
 int rsgm_set_rows_per_warp(rsgm_stream s, int32_t rows);
 
 /*

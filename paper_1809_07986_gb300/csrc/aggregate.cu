@@ -264,14 +264,21 @@ __device__ __forceinline__ void walk(int dx, int dy, int b, int k, bool line_ok,
 #pragma unroll
             for (int q = 0; q < NW; ++q) cw[q] = (q == 0 || 4 * q < w) ? cc[q] : 0xFFFFFFFFu;
             const unsigned w2 = (unsigned)w * 0x10001u;
-            unsigned run = kInf2;
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
                 unsigned c = __byte_perm(cw[i >> 1], 0u, (i & 1) ? 0x4342u : 0x4140u);
                 if (!kCheap) c = mask_pair(c, (unsigned)(2 * i) | ((unsigned)(2 * i + 1) << 16), w2);
                 P[i] = eq1(U[i], U[i + 1], c, P1x2, cap2, m2);
-                run = vmin2(run, P[i]);
             }
+            // the window's minimum as a tree: it feeds the next step's m + P2
+            unsigned mt[NR];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) mt[i] = P[i];
+#pragma unroll
+            for (int span = 1; span < NR; span *= 2)
+#pragma unroll
+                for (int i = 0; i + span < NR; i += 2 * span) mt[i] = vmin2(mt[i], mt[i + span]);
+            const unsigned run = mt[0];
             // plane words of the pixel's cells [0, round4(w))
             if (sizeof(T) == 1) {
                 unsigned *dst = (unsigned *)(plane + o);
@@ -514,8 +521,8 @@ int sweep_capacity(int cells)
     return cells <= 2 ? 2 : (cells <= 6 ? 6 : (cells <= 10 ? 10 : 18));
 }
 
-cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2, int nbits,
-                         int plane_bytes, int capacity, int hlines, cudaStream_t st)
+cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, unsigned run_mask, int P1, int P2,
+                         int nbits, int plane_bytes, int capacity, int hlines, cudaStream_t st)
 {
     LinePlan plan;
     plan.g = g;
@@ -549,7 +556,7 @@ cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask
     plan.warp_begin[0] = 0;
     for (int kk = 0; kk < 8; ++kk) {
         const int dir = order[kk];
-        if (!(path_mask & (1u << dir))) continue;
+        if (!(path_mask & run_mask & (1u << dir))) continue;
         const int lpw = kHostDY[dir] == 0 ? plan.hlines : 32;
         const long long warps =
             (long long)g.B * ((lines_per_stream(kHostDX[dir], kHostDY[dir], g.W, g.H) + lpw - 1) / lpw);

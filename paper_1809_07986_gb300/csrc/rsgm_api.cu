@@ -34,9 +34,12 @@ struct rsgm_stream_s {
     int nbits;
     int nplanes;      // enabled path directions
     int capacity;     // window cells a path-sweep lane keeps in registers (default for the radius mode)
+    int lanes;        // lanes per row of the row sweep (the common window width)
+    cudaStream_t side;            // the row sweep runs here, beside the other directions' sweep
+    cudaEvent_t fork_ev, join_ev;
     int sm_count;     // multiprocessors of the handle's device
     int tuned_cap;    // register capacity picked by rsgm_autotune / rsgm_set_schedule (0: default)
-    int tuned_hl;     // rows per horizontal warp picked by rsgm_autotune (0: default)
+    int tuned_hl;     // horizontal directions: 0 = the row sweep, 8/16/32 = rows per warp of the line sweep
     bool capturing;   // enqueueing into a group's graph: no stage-timing events
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
@@ -182,6 +185,16 @@ void free_cnn(rsgm_cnn c)
     }
 }
 
+// The row sweep's side stream and its fork / join events.
+void release_side(rsgm_stream_s *s)
+{
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->join_ev) cudaEventDestroy(s->join_ev);
+    if (s->side) cudaStreamDestroy(s->side);
+    s->fork_ev = s->join_ev = nullptr;
+    s->side = nullptr;
+}
+
 FrameParams frame_params(const rsgm_stream_s *s, const uint8_t *roles = nullptr, uint8_t all = RSGM_SLOT_REDUCED)
 {
     FrameParams fp;
@@ -237,6 +250,30 @@ int mark(rsgm_stream s, int k)
 // Census, cost, aggregation and the update: the part shared by both frame
 // kinds.  A learned frame has run the census already (the network reads it)
 // and corrects with its per-pixel measurement variance r_map.
+// Eq. 1 over every enabled direction.  By default the horizontal directions
+// run in the row sweep on the handle's side stream, forked from and joined
+// back into `st`, while the line sweep does the others; with rows = 8, 16 or
+// 32 the line sweep does all of them.
+cudaError_t launch_aggregation(rsgm_stream s, int capacity, int rows, cudaStream_t st)
+{
+    const unsigned mask = s->P.path_mask, hmask = mask & 3u;
+    const Geometry &g = s->g;
+    if (rows != 0 || hmask == 0)
+        return launch_paths(s->buf, g, mask, mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes, capacity, rows, st);
+    if ((mask & ~3u) == 0)
+        return launch_rows(s->buf, g, mask, hmask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, st);
+    cudaError_t e = cudaEventRecord(s->fork_ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->fork_ev, 0);
+    if (e == cudaSuccess)
+        e = launch_rows(s->buf, g, mask, hmask, s->P.P1, s->P.P2, s->lanes, s->plane_bytes, s->sm_count, s->side);
+    const cudaError_t e2 = launch_paths(s->buf, g, mask, mask & ~3u, s->P.P1, s->P.P2, s->nbits, s->plane_bytes,
+                                        capacity, 16, st);
+    // join even after a failed launch, so that the side stream never runs ahead
+    const cudaError_t e3 = cudaEventRecord(s->join_ev, s->side);
+    const cudaError_t e4 = e3 == cudaSuccess ? cudaStreamWaitEvent(st, s->join_ev, 0) : e3;
+    return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e4);
+}
+
 int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool census_done, const float *r_map,
                      const FrameParams &fp)
 {
@@ -250,8 +287,7 @@ int match_and_update(rsgm_stream s, const uint8_t *dl, const uint8_t *dr, bool c
     RSGM_MARK(s, 3);
     RSGM_CUDA(launch_cost(s->buf, g, s->nbits, s->st));
     RSGM_MARK(s, 4);
-    RSGM_CUDA(launch_paths(s->buf, g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes,
-                           s->tuned_cap ? s->tuned_cap : s->capacity, s->tuned_hl, s->st));
+    RSGM_CUDA(launch_aggregation(s, s->tuned_cap ? s->tuned_cap : s->capacity, s->tuned_hl, s->st));
     RSGM_MARK(s, 5);
     RSGM_CUDA(launch_update(s->buf, g, fp, r_map, s->nplanes, s->plane_bytes, s->st));
     RSGM_MARK(s, 6);
@@ -465,7 +501,21 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
                   : p->radius_mode == RSGM_RADIUS_LEARNED ? 17
                   : p->radius_mode == RSGM_RADIUS_VARIANCE ? 9
                   : (p->max_disp <= 18 ? p->max_disp : 2);
+    s->lanes = lanes_per_line(p->radius_mode == RSGM_RADIUS_FIXED     ? 2 * p->radius + 1
+                              : p->radius_mode == RSGM_RADIUS_LEARNED ? 17
+                                                                      : p->max_disp);
     s->p_reset = p->p_reset > 0.0f ? p->p_reset : (float)p->max_disp * (float)p->max_disp / 12.0f;
+    if ((e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    if ((e = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming)) != cudaSuccess) {
+        if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+        cudaStreamDestroy(s->side);
+        delete s;
+        return cuda_fail(e, "cudaEventCreateWithFlags");
+    }
     s->has_state = false;
     memset(s->slot_state, 0, sizeof(s->slot_state));
     memset(&s->buf, 0, sizeof(s->buf));
@@ -492,6 +542,7 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (rc = alloc(&b.sat, (size_t)p->batch * (p->height + 1) * (p->width + 1), all, nall)) ||
         (rc = alloc(&b.flags, n * RSGM_MAX_WINDOW_SIZES, all, nall))) {
         free_buffers(b);
+        release_side(s);
         delete s;
         return rc;
     }
@@ -501,6 +552,7 @@ int rsgm_init_stream(rsgm_stream *out, const rsgm_params *p, void *cuda_stream)
         (e = cudaMemsetAsync(b.counters, 0, 4 * sizeof(unsigned long long), s->st)) != cudaSuccess ||
         (e = cudaMemsetAsync(b.mask, 0, n, s->st)) != cudaSuccess) {
         free_buffers(b);
+        release_side(s);
         delete s;
         return cuda_fail(e, "cudaMemsetAsync");
     }
@@ -834,10 +886,12 @@ int rsgm_destroy_stream(rsgm_stream s)
     {
         DeviceGuard dg(s->device);
         cudaError_t e = cudaStreamSynchronize(s->st);
+        if (e == cudaSuccess && s->side) e = cudaStreamSynchronize(s->side);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
         free_buffers(s->buf);
         free_learned(s->lb);
         destroy_timer(s->timer);
+        release_side(s);
     }
     delete s;
     return rc;
@@ -1042,23 +1096,22 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells)
         cudaEventDestroy(e0);
         return fail(RSGM_ERR_CUDA, "cudaEventCreate");
     }
-    // candidates: the instantiated register capacities, and 8, 16 or 32 rows
-    // per horizontal warp
-    const int caps[4] = {2, 6, 10, 18}, hls[3] = {8, 16, 32};
-    const int nc = 12;
+    // candidates: the instantiated register capacities, and the row sweep or
+    // 8, 16 or 32 rows per warp of the line sweep for the horizontal directions
+    const int caps[4] = {2, 6, 10, 18}, hls[4] = {0, 8, 16, 32};
+    const int nh = (s->P.path_mask & 3u) ? 4 : 1, nc = 4 * nh;
     int best = 0, best_hl = 0;
     float best_ms = 0.0f;
     int rc = RSGM_OK;
     // Every candidate computes the same planes (each schedule is exact), so
     // re-running the aggregation on the last frame's costs changes nothing.
     for (int ci = 0; ci < nc && rc == RSGM_OK; ++ci) {
-        const int cand = caps[ci / 3], hl = hls[ci % 3];
+        const int cand = caps[ci / nh], hl = hls[ci % nh];
         float ms = 1e30f;
         for (int rep = 0; rep < 3 && rc == RSGM_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, s->st);
             if (e == cudaSuccess)
-                e = launch_paths(s->buf, s->g, s->P.path_mask, s->P.P1, s->P.P2, s->nbits, s->plane_bytes, cand, hl,
-                                 s->st);
+                e = launch_aggregation(s, cand, hl, s->st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float t = 0.0f;

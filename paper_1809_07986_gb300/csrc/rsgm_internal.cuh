@@ -179,10 +179,17 @@ cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStre
 // planes of `plane_bytes` (1 or 2) per cell.  Windows of up to `capacity`
 // cells (rounded up by sweep_capacity to 2, 6, 10 or 18) are walked in a
 // lane's registers, wider ones by the whole warp.
-// hlines: rows a warp walks for the horizontal directions (8, 16 or 32; 0 = 16).
+// path_mask numbers the planes (one per enabled direction, in bit order);
+// run_mask selects the directions this launch sweeps.  hlines: rows a warp
+// walks for the horizontal directions (8, 16 or 32; 0 = 16).
 int sweep_capacity(int cells);
-cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, int P1, int P2, int nbits,
-                         int plane_bytes, int capacity, int hlines, cudaStream_t st);
+cudaError_t launch_paths(const Buffers &b, const Geometry &g, unsigned path_mask, unsigned run_mask, int P1, int P2,
+                         int nbits, int plane_bytes, int capacity, int hlines, cudaStream_t st);
+// The two horizontal directions (run_mask bits 0 and 1) with G lanes per row
+// (lanes_per_line of the common window width).
+int lanes_per_line(int window);
+cudaError_t launch_rows(const Buffers &b, const Geometry &g, unsigned path_mask, unsigned run_mask, int P1, int P2,
+                        int lanes, int plane_bytes, int sm_count, cudaStream_t st);
 
 // Sum of the planes, winner-takes-all, Kalman correction and gate
 // (Sections 2.2-2.4).
