@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--radius", type=int, default=4)
     ap.add_argument("--schedule", type=int, default=0,
                     help="path-sweep register capacity in cells for every handle (0: autotune each handle)")
+    ap.add_argument("--rows", type=int, default=0, choices=[0, 8, 16, 32],
+                    help="with --schedule: the rows' sweep (0: the row sweep beside the line sweep, "
+                         "else rows per warp of the line sweep)")
     ap.add_argument("--handles", type=int, default=2,
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
     ap.add_argument("--learned", action="store_true",
@@ -70,6 +73,13 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-form, latency, e2e and CPU-baseline legs")
     return ap.parse_args()
+
+
+def launches_per_frame(rows: int) -> int:
+    """Kernels one reduced frame of an 8-path handle launches: splat, fill,
+    window, row scan, census, cost, the aggregation (one sweep, or the row
+    sweep beside the line sweep when rows = 0) and the update."""
+    return 8 + (rows == 0)
 
 
 def stream_seeds(rank: int, batch: int) -> list:
@@ -325,7 +335,8 @@ def mixed_group(args, dev, stream):
             m.full_frame(x["L"][0], x["R"][0])
         tick(1)
         for m in members:
-            tuned.append(rs.rsgm_autotune(m.handle))
+            rs.rsgm_autotune(m.handle)
+            tuned.append(rs.rsgm_get_schedule(m.handle))
         for k in range(2, 1 + args.warmup):
             tick(k)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -342,7 +353,8 @@ def mixed_group(args, dev, stream):
     nstreams = sum(g[0] for g in MIXED)
     return {"frames_per_s": nstreams * args.steps / el, "ms_per_tick": 1e3 * el / args.steps,
             "streams": "6x640x480/D64 + 6x1242x375/D128 + 4x1920x1080/D256",
-            "graph_launches_per_tick": 1, "sweep_capacity_tuned": tuned}
+            "graph_launches_per_tick": 1,
+            "schedule_tuned": [{"cells": c, "rows": "row sweep" if r == 0 else "%d per warp" % r} for c, r in tuned]}
 
 
 # ------------------------------------------------------------------ request loop
@@ -477,10 +489,13 @@ def run_ours(args, rank, world, local_rank):
         parts.append((rs.Stream(Ph, cs), cs, a, z))
 
     def tune(h):
+        """Sets the handle's aggregation schedule; returns (cells, rows)."""
         if args.schedule > 0:
             rs.rsgm_set_schedule(h, args.schedule)
-            return args.schedule
-        return rs.rsgm_autotune(h)
+            rs.rsgm_set_rows_per_warp(h, args.rows)
+        else:
+            rs.rsgm_autotune(h)
+        return rs.rsgm_get_schedule(h)
 
     def run_parts(frames, host=None, out=None):
         for k in frames:
@@ -542,17 +557,18 @@ def run_ours(args, rank, world, local_rank):
                          "l2": "per-step working set (ragged volumes) larger than L2"},
               "cell_updates_per_s": cells_all * N_PATHS / elapsed,
               "cells_per_frame": cells_local / (B * steps),
-              "sweep_capacity_tuned": tuned,
+              "schedule_tuned": [{"cells": c, "rows": "row sweep" if r == 0 else "%d per warp" % r}
+                                 for c, r in tuned],
               "handles": "%d handles of %s streams on %d CUDA streams" % (
                   nh, "/".join(str(cut[i + 1] - cut[i]) for i in range(nh)), nh),
-              "gpu_launches": 8 * steps * nh,
+              "gpu_launches": steps * sum(launches_per_frame(r) for _, r in tuned),
               "clocks": clk.summary()}
 
     # ---- dominant kernel: stage times with CUDA events on the launching stream
     with torch.cuda.stream(stream):
         gs.full_frame(left[0], right[0])
         run(gs.handle, range(1, 2))
-        tune(gs.handle)
+        _, gs_rows = tune(gs.handle)
         rs.rsgm_enable_stage_timing(gs.handle, True)
         rs.rsgm_stage_times(gs.handle)
         c_before = gs.counters()[1]
@@ -572,7 +588,10 @@ def run_ours(args, rank, world, local_rank):
     result["stage_ms_per_step"] = {k: v / max(st_frames, 1) for k, v in st_ms.items()}
     result["int_peaks_tops"] = dict(int_peaks, note="measured by rsgm_measure_int_peak on this GPU (scalar operations "
                                                     "per second; a packed 16-bit-pair instruction counts two)")
-    result["roofline"] = {"kernel": "k_paths (all 8 directions, one launch)", "bound": "alu", "achieved": achieved_tops,
+    agg_kernel = ("k_lines (all 8 directions, one launch)" if gs_rows else
+                  "k_lines (6 vertical and diagonal directions) beside k_rows (2 horizontal directions) "
+                  "on a forked stream: the aggregation stage")
+    result["roofline"] = {"kernel": agg_kernel, "bound": "alu", "achieved": achieved_tops,
                           "peak": int32_peak, "unit": "Tops/s", "frac": achieved_tops / int32_peak,
                           "frac_of_packed16_peak": achieved_tops / int_peaks["u16x2_mix"],
                           "traffic": (NCU_DRAM_BYTES_PER_CELL * cells_per_frame
@@ -645,6 +664,7 @@ def run_ours(args, rank, world, local_rank):
             g1.full_frame(left[0, 0], right[0, 0])
             rs.rsgm_reduced_frame(g1.handle, left[1, 0], right[1, 0], Rm[1, :1], tv[1, :1], K, BASE)
             rs.rsgm_autotune(g1.handle)
+            sched1 = rs.rsgm_get_schedule(g1.handle)
             g1.full_frame(left[0, 0], right[0, 0])
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(nframes - 1)]
@@ -663,7 +683,9 @@ def run_ours(args, rank, world, local_rank):
         g1.close()
         q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
         result["latency_ms"] = {"p50": q(0.5), "p99": q(0.99), "frames": len(lat), "streams": 1,
-                                "stage_ms": {k: v / max(n1, 1) for k, v in st1.items()}}
+                                "stage_ms": {k: v / max(n1, 1) for k, v in st1.items()},
+                                "schedule_tuned": {"cells": sched1[0], "rows": "row sweep" if sched1[1] == 0
+                                                   else "%d per warp" % sched1[1]}}
 
         # ---- after the path: 3x3 median output and moving-object boxes
         dp = rs.rsgm_default_detect_params()

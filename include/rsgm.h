@@ -328,8 +328,10 @@ int rsgm_window_offsets_noalloc(const uint32_t *windows, int32_t width, int32_t 
  * diagonal lines.  The rows go to a row sweep or to the line sweep (see
  * rsgm_set_rows_per_warp).  rsgm_autotune times the aggregation on the
  * handle's latest frame with each capacity (2, 6, 10, 18 cells) and each way
- * of sweeping the rows and keeps the fastest for later frames (the capacity
- * is written to *cells if not NULL).
+ * of sweeping the rows, each timed as a frame runs it (behind the cost
+ * kernel, which it re-runs on the unchanged census and windows), and keeps
+ * the fastest for later frames (the capacity is written to *cells if not
+ * NULL; rsgm_get_schedule reads both choices).
  * Results do not depend on the choice; only speed does.  Requires a
  * processed frame; synchronises.
  */
@@ -337,8 +339,8 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells);
 
 /* Sets the register capacity by hand: 0 = the radius mode's default
  * (2 radius + 1 for fixed windows), else 1 .. 32 cells, rounded up to the
- * nearest of 2, 6, 10, 18; the row count returns to its default (16).
- * Results do not depend on it. */
+ * nearest of 2, 6, 10, 18; the rows return to their default sweep (the
+ * row sweep, see rsgm_set_rows_per_warp).  Results do not depend on it. */
 int rsgm_set_schedule(rsgm_stream s, int32_t cells);
 
 /* How the horizontal directions are swept: 0 (the default) by the row
@@ -346,6 +348,19 @@ int rsgm_set_schedule(rsgm_stream s, int32_t cells);
  * beside the other directions' sweep; 8, 16 or 32 by the line sweep with
  * that many rows per warp.  Results do not depend on it. */
 int rsgm_set_rows_per_warp(rsgm_stream s, int32_t rows);
+
+/* The schedule later frames use: *cells = the register capacity (2, 6, 10
+ * or 18), *rows = the rows' sweep (0: the row sweep, else rows per warp of
+ * the line sweep), as set by rsgm_autotune, rsgm_set_schedule and
+ * rsgm_set_rows_per_warp.  Either pointer may be NULL. */
+int rsgm_get_schedule(rsgm_stream s, int32_t *cells, int32_t *rows);
+
+/* What the latest rsgm_autotune measured: *count = the candidates it timed
+ * (0 before the first call, 16 with horizontal directions, else 4); the
+ * first min(n, *count) of them are written as (cells[i], rows[i], ms[i]),
+ * ms = its time per aggregation launch.  n = 0 reads the count alone;
+ * otherwise the three arrays must hold n entries. */
+int rsgm_autotune_times(rsgm_stream s, int32_t *cells, int32_t *rows, float *ms, int32_t n, int32_t *count);
 
 /*
  * A group advances several handles of possibly different geometry by one

@@ -123,6 +123,10 @@ SIGNATURES = {
     "rsgm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rsgm_set_rows_per_warp": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "rsgm_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "rsgm_autotune_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int32)]),
     "rsgm_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int32]),
     "rsgm_group_reduced_frame": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                                 ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
@@ -356,6 +360,23 @@ def rsgm_set_schedule(h: int, cells: int):
 
 def rsgm_set_rows_per_warp(h: int, rows: int):
     _check(lib().rsgm_set_rows_per_warp(h, rows), "rsgm_set_rows_per_warp")
+
+
+def rsgm_autotune_times(h: int) -> list:
+    """[(cells, rows, ms per launch)] of every candidate the latest rsgm_autotune timed."""
+    n = ctypes.c_int32()
+    _check(lib().rsgm_autotune_times(h, None, None, None, 0, ctypes.byref(n)), "rsgm_autotune_times")
+    k = n.value
+    c, r, m = (ctypes.c_int32 * max(k, 1))(), (ctypes.c_int32 * max(k, 1))(), (ctypes.c_float * max(k, 1))()
+    _check(lib().rsgm_autotune_times(h, c, r, m, k, ctypes.byref(n)), "rsgm_autotune_times")
+    return [(c[i], r[i], m[i]) for i in range(k)]
+
+
+def rsgm_get_schedule(h: int) -> tuple:
+    """(register capacity in cells, rows: 0 = row sweep, else rows per warp)."""
+    c, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().rsgm_get_schedule(h, ctypes.byref(c), ctypes.byref(r)), "rsgm_get_schedule")
+    return c.value, r.value
 
 
 def rsgm_group_create(handles) -> int:

@@ -40,6 +40,9 @@ struct rsgm_stream_s {
     int sm_count;     // multiprocessors of the handle's device
     int tuned_cap;    // register capacity picked by rsgm_autotune / rsgm_set_schedule (0: default)
     int tuned_hl;     // horizontal directions: 0 = the row sweep, 8/16/32 = rows per warp of the line sweep
+    int ntimed;                        // candidates the latest rsgm_autotune timed
+    int timed_cap[16], timed_hl[16];   // their schedules
+    float timed_ms[16];                // and their times, ms per launch
     bool capturing;   // enqueueing into a group's graph: no stage-timing events
     int plane_bytes;  // 1 if every L_r fits in 8 bits (nbits + P2 <= 255), else 2
     float p_reset;
@@ -1084,40 +1087,79 @@ int rsgm_set_rows_per_warp(rsgm_stream s, int32_t rows)
     return RSGM_OK;
 }
 
+int rsgm_get_schedule(rsgm_stream s, int32_t *cells, int32_t *rows)
+{
+    if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
+    if (cells) *cells = s->tuned_cap ? s->tuned_cap : sweep_capacity(s->capacity);
+    if (rows) *rows = s->tuned_hl;
+    return RSGM_OK;
+}
+
+int rsgm_autotune_times(rsgm_stream s, int32_t *cells, int32_t *rows, float *ms, int32_t n, int32_t *count)
+{
+    if (!s || !count) return fail(RSGM_ERR_INVALID_ARG, "NULL handle or count");
+    if (n < 0 || (n > 0 && (!cells || !rows || !ms))) return fail(RSGM_ERR_INVALID_ARG, "bad output arrays");
+    *count = s->ntimed;
+    for (int i = 0; i < s->ntimed && i < n; ++i) {
+        cells[i] = s->timed_cap[i];
+        rows[i] = s->timed_hl[i];
+        ms[i] = s->timed_ms[i];
+    }
+    return RSGM_OK;
+}
+
 int rsgm_autotune(rsgm_stream s, int32_t *cells)
 {
     if (!s) return fail(RSGM_ERR_INVALID_ARG, "NULL handle");
     if (!s->has_state) return fail(RSGM_ERR_NO_STATE, "autotuning needs a processed frame");
     DeviceGuard dg(s->device);
     if (!dg.ok) return fail(RSGM_ERR_CUDA, "cannot select the handle's device");
-    cudaEvent_t e0, e1;
-    RSGM_CUDA(cudaEventCreate(&e0));
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return fail(RSGM_ERR_CUDA, "cudaEventCreate");
-    }
+    s->ntimed = 0;
+    // Each candidate is timed as a frame runs it: the cost kernel, then the
+    // aggregation between two events (as the stage timer brackets it), kReps
+    // times queued back to back behind one untimed round, so that the host's
+    // cost of issuing the launches stays hidden behind GPU work.  Launches of
+    // the aggregation alone, back to back, ran slower than inside frames and
+    // misjudged the row sweep.  The cost kernel rewrites the same costs and
+    // metadata from the unchanged census and windows, and every schedule
+    // writes the same planes, so the handle's buffers end as they were.
+    constexpr int kReps = 3;
+    cudaEvent_t ev[2 * kReps] = {};
+    int rc = RSGM_OK;
+    for (int i = 0; i < 2 * kReps && rc == RSGM_OK; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) rc = fail(RSGM_ERR_CUDA, "cudaEventCreate");
     // candidates: the instantiated register capacities, and the row sweep or
     // 8, 16 or 32 rows per warp of the line sweep for the horizontal directions
     const int caps[4] = {2, 6, 10, 18}, hls[4] = {0, 8, 16, 32};
     const int nh = (s->P.path_mask & 3u) ? 4 : 1, nc = 4 * nh;
     int best = 0, best_hl = 0;
     float best_ms = 0.0f;
-    int rc = RSGM_OK;
-    // Every candidate computes the same planes (each schedule is exact), so
-    // re-running the aggregation on the last frame's costs changes nothing.
     for (int ci = 0; ci < nc && rc == RSGM_OK; ++ci) {
         const int cand = caps[ci / nh], hl = hls[ci % nh];
         float ms = 1e30f;
-        for (int rep = 0; rep < 3 && rc == RSGM_OK; ++rep) {
-            cudaError_t e = cudaEventRecord(e0, s->st);
-            if (e == cudaSuccess)
-                e = launch_aggregation(s, cand, hl, s->st);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s->st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float t = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        for (int trial = 0; trial < 2 && rc == RSGM_OK; ++trial) {
+            cudaError_t e = launch_cost(s->buf, s->g, s->nbits, s->st);
+            if (e == cudaSuccess) e = launch_aggregation(s, cand, hl, s->st);
+            for (int rep = 0; rep < kReps && e == cudaSuccess; ++rep) {
+                e = launch_cost(s->buf, s->g, s->nbits, s->st);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[2 * rep], s->st);
+                if (e == cudaSuccess) e = launch_aggregation(s, cand, hl, s->st);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[2 * rep + 1], s->st);
+            }
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[2 * kReps - 1]);
+            float total = 0.0f;
+            for (int rep = 0; rep < kReps && e == cudaSuccess; ++rep) {
+                float t = 0.0f;
+                e = cudaEventElapsedTime(&t, ev[2 * rep], ev[2 * rep + 1]);
+                total += t;
+            }
             if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
-            if (t < ms) ms = t;
+            if (total / kReps < ms) ms = total / kReps;
+        }
+        if (rc == RSGM_OK) {
+            s->timed_cap[ci] = cand;
+            s->timed_hl[ci] = hl;
+            s->timed_ms[ci] = ms;
         }
         if (rc == RSGM_OK && (best == 0 || ms < best_ms)) {
             best = cand;
@@ -1125,9 +1167,10 @@ int rsgm_autotune(rsgm_stream s, int32_t *cells)
             best_ms = ms;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (int i = 0; i < 2 * kReps; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
     if (rc) return rc;
+    s->ntimed = nc;
     s->tuned_cap = best;
     s->tuned_hl = best_hl;
     if (cells) *cells = best;

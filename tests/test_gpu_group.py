@@ -182,6 +182,17 @@ def test_every_row_schedule_gives_the_same_aggregation(rs, mask):
         with pytest.raises(rs.RsgmError) as e:
             rs.rsgm_set_rows_per_warp(s.handle, 12)
         assert e.value.code == rs.RSGM_ERR_INVALID_ARG
+        # the getter reports what later frames use
+        assert rs.rsgm_get_schedule(s.handle) == (10, 0)      # radius 4: 9 cells, rounded up; row sweep
+        rs.rsgm_set_rows_per_warp(s.handle, 16)
+        rs.rsgm_set_schedule(s.handle, 5)                      # resets the rows to the row sweep
+        assert rs.rsgm_get_schedule(s.handle) == (6, 0)
+        rs.rsgm_set_rows_per_warp(s.handle, 32)
+        assert rs.rsgm_get_schedule(s.handle) == (6, 32)
+        s.full_frame(L[:, 0].cuda().contiguous(), R[:, 0].cuda().contiguous())
+        rs.rsgm_autotune(s.handle)
+        cells, rows = rs.rsgm_get_schedule(s.handle)
+        assert cells in (2, 6, 10, 18) and rows in ((0, 8, 16, 32) if mask & 3 else (0,))
 
 
 @pytest.mark.parametrize("radius", [2, 4, 8])
