@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--rows", type=int, default=0, choices=[0, 8, 16, 32],
                     help="with --schedule: the rows' sweep (0: the row sweep beside the line sweep, "
                          "else rows per warp of the line sweep)")
+    ap.add_argument("--priority", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the first handle's CUDA stream gets a higher priority than the others'; "
+                         "0: equal priorities")
     ap.add_argument("--handles", type=int, default=2,
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
     ap.add_argument("--learned", action="store_true",
@@ -487,7 +490,11 @@ def run_ours(args, rank, world, local_rank):
     for i in range(nh):
         a, z = cut[i], cut[i + 1]
         Ph = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=z - a)
-        cs = torch.cuda.Stream(dev)
+        # The first handle's CUDA stream outranks the others (--priority 1):
+        # its kernels take the SMs first and the others fill what is left, so
+        # the handles never fall into step (both sweeping, then both
+        # updating), which with equal priorities happened in some runs.
+        cs = torch.cuda.Stream(dev, priority=-1 if (args.priority and i == 0) else 0)
         parts.append((rs.Stream(Ph, cs), cs, a, z))
 
     def tune(h):
@@ -561,8 +568,9 @@ def run_ours(args, rank, world, local_rank):
               "cells_per_frame": cells_local / (B * steps),
               "schedule_tuned": [{"cells": c, "rows": "row sweep" if r == 0 else "%d per warp" % r}
                                  for c, r in tuned],
-              "handles": "%d handles of %s streams on %d CUDA streams" % (
-                  nh, "/".join(str(cut[i + 1] - cut[i]) for i in range(nh)), nh),
+              "handles": "%d handles of %s streams on %d CUDA streams%s" % (
+                  nh, "/".join(str(cut[i + 1] - cut[i]) for i in range(nh)), nh,
+                  ", the first at a higher stream priority" if args.priority and nh > 1 else ""),
               "gpu_launches": steps * sum(launches_per_frame(r) for _, r in tuned),
               "clocks": clk.summary()}
 

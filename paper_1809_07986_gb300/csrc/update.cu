@@ -89,7 +89,7 @@ __device__ __forceinline__ void sum_planes(const uint16_t *__restrict__ planes, 
 // reset to the measurement, else K = p_pred / (p_pred + r), d = d_pred + K nu,
 // p = (1 - K)^2 p_pred + K^2 r.
 template <typename T>
-__global__ void __launch_bounds__(kUpdWarps * 32, 12) k_update(const T *__restrict__ planes, long long plane_stride,
+__global__ void __launch_bounds__(kUpdWarps * 32, 16) k_update(const T *__restrict__ planes, long long plane_stride,
                                                         int nplanes, uint16_t *__restrict__ S,
                                                         const uint2 *__restrict__ meta,
                                                         const uint8_t *__restrict__ cls,
