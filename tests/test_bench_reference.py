@@ -56,3 +56,12 @@ def test_gpus_flag_without_a_launcher_starts_one_rank_per_gpu(monkeypatch):
     assert cmd[cmd.index("--nproc-per-node") + 1] == "4" and cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
     assert cmd[-4:] == ["--gpus", "4", "--steps", "3"]
     assert bench.host_cores() >= 1
+
+
+def test_launch_count_per_frame_follows_the_schedule():
+    # splat, fill, window, row scan, census, cost, sweep(s), update
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.launches_per_frame(0) == 9          # row sweep beside the line sweep
+    for rows in (8, 16, 32):
+        assert bench.launches_per_frame(rows) == 8   # one line sweep for every direction
