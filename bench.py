@@ -65,7 +65,7 @@ def parse():
                     help="with --schedule: the rows' sweep (0: the row sweep beside the line sweep, "
                          "else rows per warp of the line sweep)")
     ap.add_argument("--priority", type=int, default=1, choices=[0, 1],
-                    help="1 (default): the first handle's CUDA stream gets a higher priority than the others'; "
+                    help="1 (default): each handle's CUDA stream gets a higher priority than the next one's; "
                          "0: equal priorities")
     ap.add_argument("--handles", type=int, default=2,
                     help="the GPU's streams are split over this many handles on as many CUDA streams")
@@ -490,11 +490,12 @@ def run_ours(args, rank, world, local_rank):
     for i in range(nh):
         a, z = cut[i], cut[i + 1]
         Ph = rs.rsgm_default_params(W, H, max_disp=D, radius=args.radius, batch=z - a)
-        # The first handle's CUDA stream outranks the others (--priority 1):
-        # its kernels take the SMs first and the others fill what is left, so
+        # Each handle's CUDA stream outranks the next one's (--priority 1):
+        # the first handle's kernels take the SMs first and the others fill
+        # what is left, in order, so
         # the handles never fall into step (both sweeping, then both
         # updating), which with equal priorities happened in some runs.
-        cs = torch.cuda.Stream(dev, priority=-1 if (args.priority and i == 0) else 0)
+        cs = torch.cuda.Stream(dev, priority=-(nh - 1 - i) if args.priority else 0)
         parts.append((rs.Stream(Ph, cs), cs, a, z))
 
     def tune(h):
@@ -570,7 +571,7 @@ def run_ours(args, rank, world, local_rank):
                                  for c, r in tuned],
               "handles": "%d handles of %s streams on %d CUDA streams%s" % (
                   nh, "/".join(str(cut[i + 1] - cut[i]) for i in range(nh)), nh,
-                  ", the first at a higher stream priority" if args.priority and nh > 1 else ""),
+                  ", each at a higher stream priority than the next" if args.priority and nh > 1 else ""),
               "gpu_launches": steps * sum(launches_per_frame(r) for _, r in tuned),
               "clocks": clk.summary()}
 
