@@ -99,15 +99,16 @@ __device__ __forceinline__ void band_load8(const unsigned *band, int t, int pad,
 // under the cheap masking, so saturating keeps every result).
 __device__ __forceinline__ unsigned sat8(unsigned x) { return vmin2(x, 0x00FF00FFu); }
 
-// Walks 32 adjacent lines of one direction.
+// Walks this lane's path line (the warp walks up to 32 lines of one
+// direction and stream in lockstep, placed by the caller).
 //
 // Narrow pixels (window width <= 2 NR) are done by the line's own lane, the
 // window in NR packed registers: slot k holds the loss at d = lo + k.  When
 // the window moves by at most 2 against the predecessor's, the predecessor's
 // losses are realigned in registers; otherwise they go through the lane's
 // band in shared memory.  Wide pixels (the full-range windows of resets and
-// pixels without a prediction) are done by the whole warp, 4 cells per lane,
-// with the predecessor's losses in the line's band.  A band holds a window at
+// pixels without a prediction) are done by the whole warp, with the
+// predecessor's losses in the line's band.  A band holds a window at
 // slots [0, w) with +inf on [-pad, 0) and on [round4(w), round4(w) + pad);
 // reads that can see no slot of [0, w) take +inf without loading.
 //

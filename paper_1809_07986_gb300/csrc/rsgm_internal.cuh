@@ -45,9 +45,11 @@ struct SplatArgs {
     SlotRoles role;  // only RSGM_SLOT_REDUCED streams are predicted
 };
 
-// Launch plan of the aggregation kernel: the enabled directions in launch
-// order, the first warp of each (a warp walks 32 adjacent path lines of one
-// stream), the plane each writes, and the per-lane band of shared memory.
+// Launch plan of the line sweep: the directions it runs in launch order,
+// the first warp of each (a warp walks up to 32 path lines of one stream:
+// rows spread across the image, or 8 groups of 4 adjacent vertical or
+// diagonal lines), the plane each writes, and the per-lane band of shared
+// memory.
 constexpr int kLineWarps = 4;  // warps per block of the aggregation kernel
 struct LinePlan {
     Geometry g;
@@ -175,8 +177,9 @@ cudaError_t launch_census(const Buffers &b, const Geometry &g, const uint8_t *le
                           const uint8_t *right, int cw, int ch, cudaStream_t st);
 cudaError_t launch_cost(const Buffers &b, const Geometry &g, int nbits, cudaStream_t st);
 
-// Aggregation, Eq. 1 (Section 2.2): every enabled direction in one launch,
-// planes of `plane_bytes` (1 or 2) per cell.  Windows of up to `capacity`
+// Aggregation, Eq. 1 (Section 2.2), the line sweep: the directions of
+// run_mask in one launch, one lane per path line, planes of `plane_bytes`
+// (1 or 2) per cell.  Windows of up to `capacity`
 // cells (rounded up by sweep_capacity to 2, 6, 10 or 18) are walked in a
 // lane's registers, wider ones by the whole warp.
 // path_mask numbers the planes (one per enabled direction, in bit order);
