@@ -49,6 +49,9 @@ FRAME_OPS_PER_CELL = 10 * N_PATHS + 2
 # rows per warp, one 32-stream launch of reduced frame 2 (188,694,827 cells):
 # 3,544,918,784 B read + 2,052,158,464 B written.
 NCU_DRAM_BYTES_PER_CELL = (3544918784 + 2052158464) / 188694827
+# the configuration that figure was captured on: streams per launch, register
+# capacity and rows per warp; other configurations report no traffic
+NCU_DRAM_CONFIG = (32, 10, 16)
 
 
 def parse():
@@ -579,7 +582,7 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         gs.full_frame(left[0], right[0])
         run(gs.handle, range(1, 2))
-        _, gs_rows = tune(gs.handle)
+        gs_cells, gs_rows = tune(gs.handle)
         rs.rsgm_enable_stage_timing(gs.handle, True)
         rs.rsgm_stage_times(gs.handle)
         c_before = gs.counters()[1]
@@ -606,7 +609,8 @@ def run_ours(args, rank, world, local_rank):
                           "peak": int32_peak, "unit": "Tops/s", "frac": achieved_tops / int32_peak,
                           "frac_of_packed16_peak": achieved_tops / int_peaks["u16x2_mix"],
                           "traffic": (NCU_DRAM_BYTES_PER_CELL * cells_per_frame
-                                      if NCU_DRAM_BYTES_PER_CELL else None),
+                                      if NCU_DRAM_BYTES_PER_CELL and (B, gs_cells, gs_rows) == NCU_DRAM_CONFIG
+                                      else None),
                           "traffic_unit": "bytes per launch (ncu per-cell figure of a 32-stream launch x this launch's cells)",
                           "peak_source": "measured: int32 add/min throughput (the slower of the two), "
                                          "rsgm_measure_int_peak",
